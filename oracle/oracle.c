@@ -1,0 +1,402 @@
+/* oracle.c -- plain, slow, single-threaded CPU oracle for the RIS hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this file; the product path never does.
+ * It shares no code, header or table with the CUDA library: every definition
+ * below is written out here from the paper (GreediRIS, arXiv 2408.10982) and,
+ * for the random stream, from the Philox paper.
+ *
+ * Readings of the paper that this file fixes (the paper is silent on them):
+ *  - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = 64-bit
+ *    seed split (lo, hi); counters carry a domain tag in word 3:
+ *      ROOT (s, 0, 0, 1) lane 0 ; IC coin (s, e>>2, e>>34, 2) lane e&3 ;
+ *      LT draw (s, v, 0, 3) lane 0 ; partition (v, 0, 0, 4) lane 0.
+ *  - uniform choice of x in [0, N) from a 32-bit draw r: (r * N) >> 32.
+ *  - IC edge e is live iff its coin < w[e]; LT vertex v picks the first
+ *    in-edge (CSR order) whose running weight sum exceeds its draw.
+ *  - greedy ties go to the smallest vertex id; zero gain ends the greedy.
+ *  - RandGreedi streams seeds in (rank j, partition p) order; bucket b has
+ *    guess l*(1+delta)^b with l = max_v |S(v)|, and accepts a subset whose
+ *    gain is >= ceil(guess / (2k)); B = least b >= 1 with (1+delta)^b >= k.
+ * Floating point appears only in those thresholds (IEEE double, repeated
+ * multiplication, no pow/log) so both sides can reproduce them exactly.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random numbers: */
+/* as easy as 1, 2, 3", SC'11: ten rounds of two 32x32->64 multiplies with   */
+/* a Weyl-sequence key schedule.                                             */
+/* ------------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;   /* multiplier M0 */
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;   /* multiplier M1 */
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;                          /* Weyl constants */
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+enum { TAG_ROOT = 1, TAG_IC = 2, TAG_LT = 3, TAG_PART = 4 };
+
+static uint32_t draw(uint64_t seed, uint32_t a, uint32_t b, uint32_t c,
+                     uint32_t tag, int lane) {
+    uint32_t ctr[4] = {a, b, c, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox(ctr, key, out);
+    return out[lane];
+}
+
+/* Sample s picks its source uniformly from V (Sec. 2.1, Sample step 1). */
+uint32_t orc_root(uint64_t seed, uint32_t s, int64_t n) {
+    uint32_t r = draw(seed, s, 0, 0, TAG_ROOT, 0);
+    return (uint32_t)(((uint64_t)r * (uint64_t)n) >> 32);
+}
+
+/* The 32-bit coin of in-edge e in sample s (IC live-edge world, Def. 3). */
+uint32_t orc_ic_coin(uint64_t seed, uint32_t s, int64_t e) {
+    uint64_t ue = (uint64_t)e;
+    return draw(seed, s, (uint32_t)(ue >> 2), (uint32_t)(ue >> 34), TAG_IC, (int)(ue & 3u));
+}
+
+/* The 32-bit draw vertex v uses to pick its live in-edge in sample s (LT). */
+uint32_t orc_lt_draw(uint64_t seed, uint32_t s, uint32_t v) {
+    return draw(seed, s, v, 0, TAG_LT, 0);
+}
+
+/* Uniform random vertex partition into P parts (Alg. 3, "Partition V"). */
+int32_t orc_part_of(uint64_t pseed, uint32_t v, int32_t P) {
+    uint32_t r = draw(pseed, v, 0, 0, TAG_PART, 0);
+    return (int32_t)(((uint64_t)r * (uint64_t)P) >> 32);
+}
+
+void orc_partition(int64_t n, int32_t P, uint64_t pseed, int32_t *part) {
+    for (int64_t v = 0; v < n; ++v) part[v] = orc_part_of(pseed, (uint32_t)v, P);
+}
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One RRR set (Def. 3; Sec. 2.1 "Sample"): all vertices with a path to the */
+/* root in the random live-edge subgraph, found by BFS over in-edges.  Each */
+/* in-edge of each visited vertex gets its coin exactly once.  Writes the   */
+/* members to out[] in discovery order, returns the count.                  */
+/* visited[] (n bytes) must be all zero and is left all zero.               */
+/* ------------------------------------------------------------------------ */
+int64_t orc_sample_ic_one(int64_t n, const int64_t *in_off, const int32_t *in_src,
+                          const uint32_t *w, uint64_t seed, uint32_t s,
+                          uint8_t *visited, int32_t *out, int64_t *examined) {
+    uint32_t root = orc_root(seed, s, n);
+    int64_t tail = 0;
+    out[tail++] = (int32_t)root;
+    visited[root] = 1;
+    for (int64_t head = 0; head < tail; ++head) {
+        int32_t v = out[head];
+        for (int64_t e = in_off[v]; e < in_off[v + 1]; ++e) {
+            ++*examined;
+            if (orc_ic_coin(seed, s, e) < w[e]) {
+                int32_t u = in_src[e];
+                if (!visited[u]) {
+                    visited[u] = 1;
+                    out[tail++] = u;
+                }
+            }
+        }
+    }
+    for (int64_t t = 0; t < tail; ++t) visited[out[t]] = 0;
+    return tail;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One LT RRR set.  In the LT live-edge world each vertex keeps at most one */
+/* in-edge, chosen with probability equal to its weight (weights of a       */
+/* vertex sum to at most 1, Sec. 2).  The reverse-reachable set of the root */
+/* is then the backward chain root <- pick(root) <- ... which stops at a    */
+/* vertex that picks nothing or at an already-visited vertex.  Writes the   */
+/* chain in walk order, returns its length.                                 */
+/* ------------------------------------------------------------------------ */
+int64_t orc_sample_lt_one(int64_t n, const int64_t *in_off, const int32_t *in_src,
+                          const uint32_t *w, uint64_t seed, uint32_t s,
+                          uint8_t *visited, int32_t *out, int64_t *examined) {
+    uint32_t cur = orc_root(seed, s, n);
+    int64_t len = 0;
+    out[len++] = (int32_t)cur;
+    visited[cur] = 1;
+    for (;;) {
+        uint32_t x = orc_lt_draw(seed, s, cur);
+        uint64_t run = 0;
+        int64_t pick = -1;
+        for (int64_t e = in_off[cur]; e < in_off[cur + 1]; ++e) {
+            ++*examined;
+            run += w[e];
+            if ((uint64_t)x < run) { pick = e; break; }
+        }
+        if (pick < 0) break;
+        int32_t u = in_src[pick];
+        if (visited[u]) break;
+        visited[u] = 1;
+        out[len++] = u;
+        cur = (uint32_t)u;
+    }
+    for (int64_t t = 0; t < len; ++t) visited[out[t]] = 0;
+    return len;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sample(G, count) for ids first .. first+count-1 (Alg. 1 "Sample"; each    */
+/* sample keeps its id, Sec. 3.2).  Output: CSR by sample id; members sorted */
+/* ascending unless keep_order != 0 (then discovery / walk order).  Arrays   */
+/* are malloc'd here and released with orc_free.  model 0 = IC, 1 = LT.      */
+/* Returns 0, or -1 on allocation failure.                                   */
+/* ------------------------------------------------------------------------ */
+int orc_sample(int model, int64_t n, const int64_t *in_off, const int32_t *in_src,
+               const uint32_t *w, uint64_t seed, uint64_t first, uint64_t count,
+               int keep_order, int64_t **set_off_out, int32_t **members_out,
+               int64_t *total_out, int64_t *examined_out) {
+    uint8_t *visited = (uint8_t *)calloc((size_t)n, 1);
+    int32_t *buf = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t *set_off = (int64_t *)malloc((size_t)(count + 1) * sizeof(int64_t));
+    int64_t cap = 1024, total = 0, examined = 0;
+    int32_t *members = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    if (!visited || !buf || !set_off || !members) goto fail;
+    set_off[0] = 0;
+    for (uint64_t j = 0; j < count; ++j) {
+        uint32_t s = (uint32_t)(first + j);
+        int64_t len = model == 0
+            ? orc_sample_ic_one(n, in_off, in_src, w, seed, s, visited, buf, &examined)
+            : orc_sample_lt_one(n, in_off, in_src, w, seed, s, visited, buf, &examined);
+        if (!keep_order) qsort(buf, (size_t)len, sizeof(int32_t), cmp_i32);
+        if (total + len > cap) {
+            while (total + len > cap) cap *= 2;
+            int32_t *grown = (int32_t *)realloc(members, (size_t)cap * sizeof(int32_t));
+            if (!grown) goto fail;
+            members = grown;
+        }
+        memcpy(members + total, buf, (size_t)len * sizeof(int32_t));
+        total += len;
+        set_off[j + 1] = total;
+    }
+    free(visited);
+    free(buf);
+    *set_off_out = set_off;
+    *members_out = members;
+    *total_out = total;
+    *examined_out = examined;
+    return 0;
+fail:
+    free(visited); free(buf); free(set_off); free(members);
+    return -1;
+}
+
+void orc_free(void *p) { free(p); }
+
+/* ------------------------------------------------------------------------ */
+/* Covering subsets S(v) = { i : v in R(i) } (Sec. 3.2, max-k-cover          */
+/* formulation; the all-to-all of Alg. 3 gathers exactly these rows).        */
+/* set_ids of each vertex come out in ascending set id.                      */
+/* ------------------------------------------------------------------------ */
+int orc_invert(int64_t n, int64_t theta, const int64_t *set_off, const int32_t *members,
+               int64_t *vtx_off, int32_t *set_ids) {
+    int64_t *cursor = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!cursor) return -1;
+    for (int64_t t = 0; t < set_off[theta]; ++t) cursor[members[t] + 1]++;
+    vtx_off[0] = 0;
+    for (int64_t v = 0; v < n; ++v) vtx_off[v + 1] = vtx_off[v] + cursor[v + 1];
+    for (int64_t v = 0; v < n; ++v) cursor[v] = vtx_off[v];
+    for (int64_t i = 0; i < theta; ++i)
+        for (int64_t t = set_off[i]; t < set_off[i + 1]; ++t)
+            set_ids[cursor[members[t]]++] = (int32_t)i;
+    free(cursor);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Standard greedy max-k-cover (Sec. 3.2: repeatedly take the covering      */
+/* subset of largest marginal gain).  Candidates are the ascending vertex   */
+/* list cand[0..ncand) when cand is non-NULL (the local greedy of a         */
+/* partition V_p, Alg. 4), else all of V; the universe is {0..theta-1}.     */
+/* counts[v] is the marginal gain |S(v) \ covered|, kept exact by           */
+/* decrementing the members of every newly covered set.                     */
+/* Returns 0, or -1 on allocation failure.                                  */
+/* ------------------------------------------------------------------------ */
+int orc_greedy(int64_t n, int64_t theta, const int64_t *set_off, const int32_t *members,
+               const int64_t *vtx_off, const int32_t *set_ids, int32_t k,
+               const int32_t *cand, int64_t ncand, int32_t *seeds, int64_t *gains,
+               int32_t *nseeds, int64_t *coverage) {
+    int64_t *counts = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    uint8_t *covered = (uint8_t *)calloc((size_t)theta + 1, 1);
+    if (!counts || !covered) { free(counts); free(covered); return -1; }
+    for (int64_t v = 0; v < n; ++v) counts[v] = vtx_off[v + 1] - vtx_off[v];
+    int64_t cov = 0;
+    int32_t picked = 0;
+    for (int32_t j = 0; j < k; ++j) {
+        int64_t best = -1, best_gain = 0;
+        int64_t span = cand ? ncand : n;
+        for (int64_t c = 0; c < span; ++c) {
+            int64_t v = cand ? cand[c] : c;
+            if (counts[v] > best_gain) { best = v; best_gain = counts[v]; }
+        }
+        if (best < 0) break;                 /* every remaining gain is zero */
+        seeds[picked] = (int32_t)best;
+        gains[picked] = best_gain;
+        ++picked;
+        cov += best_gain;
+        for (int64_t t = vtx_off[best]; t < vtx_off[best + 1]; ++t) {
+            int32_t i = set_ids[t];
+            if (covered[i]) continue;
+            covered[i] = 1;
+            for (int64_t q = set_off[i]; q < set_off[i + 1]; ++q) counts[members[q]]--;
+        }
+    }
+    *nseeds = picked;
+    *coverage = cov;
+    free(counts);
+    free(covered);
+    return 0;
+}
+
+/* Number of buckets B = ceil(log_{1+delta}(u/l)) with u/l = k (Alg. 5;        */
+/* u/l = k per the runtime analysis of Sec. 3.4), taken as the least b >= 1    */
+/* with (1+delta)^b >= k, the power formed by repeated multiplication.        */
+int32_t orc_num_buckets(int32_t k, double delta) {
+    double x = 1.0;
+    int32_t b = 0;
+    while (x < (double)k) { x *= 1.0 + delta; ++b; }
+    return b < 1 ? 1 : b;
+}
+
+/* Integer acceptance threshold of each bucket: ceil(l (1+delta)^b / (2k)). */
+void orc_bucket_thresholds(int64_t l, int32_t k, double delta, int32_t B, int64_t *thr) {
+    double guess = (double)l;
+    for (int32_t b = 0; b < B; ++b) {
+        thr[b] = (int64_t)ceil(guess / (2.0 * (double)k));
+        guess *= 1.0 + delta;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Streaming max-k-cover at the receiver (Alg. 5).  Elements arrive in the  */
+/* order given by stream[0..nstream); each is a vertex id x carrying S(x).  */
+/* Every bucket b, independently, appends x when it holds fewer than k      */
+/* seeds and |S(x) \ C_b| >= thr[b].  Outputs per-bucket coverage |C_b|,    */
+/* seed counts, seeds (B*k) and marginal gains (B*k).                       */
+/* ------------------------------------------------------------------------ */
+int orc_stream_buckets(int64_t theta, const int64_t *vtx_off, const int32_t *set_ids,
+                       const int32_t *stream, int64_t nstream, int32_t k, int32_t B,
+                       const int64_t *thr, int64_t *bucket_cov, int32_t *bucket_n,
+                       int32_t *bucket_seeds, int64_t *bucket_gains) {
+    uint8_t *cov = (uint8_t *)calloc((size_t)B * (size_t)(theta + 1), 1);
+    if (!cov) return -1;
+    for (int32_t b = 0; b < B; ++b) { bucket_cov[b] = 0; bucket_n[b] = 0; }
+    for (int64_t q = 0; q < nstream; ++q) {
+        int32_t x = stream[q];
+        for (int32_t b = 0; b < B; ++b) {
+            if (bucket_n[b] >= k) continue;
+            uint8_t *C = cov + (size_t)b * (size_t)(theta + 1);
+            int64_t gain = 0;
+            for (int64_t t = vtx_off[x]; t < vtx_off[x + 1]; ++t) gain += !C[set_ids[t]];
+            if (gain < thr[b]) continue;
+            for (int64_t t = vtx_off[x]; t < vtx_off[x + 1]; ++t) C[set_ids[t]] = 1;
+            bucket_seeds[(int64_t)b * k + bucket_n[b]] = x;
+            bucket_gains[(int64_t)b * k + bucket_n[b]] = gain;
+            bucket_n[b]++;
+            bucket_cov[b] += gain;
+        }
+    }
+    free(cov);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* RandGreedi max-k-cover with streaming aggregation and truncation         */
+/* (Alg. 3 partition, Alg. 4 local greedy + final compare, Alg. 5 stream,   */
+/* Sec. 3.3.2 truncation: each partition computes all k local seeds and     */
+/* streams only its first `trunc`).  The partitions run one after another. */
+/* Outputs:                                                                 */
+/*   local_seeds/local_gains [P*k], local_n [P], local_cov [P]              */
+/*   B, thr [B], bucket_cov [B], bucket_n [B], bucket_seeds [B*k],          */
+/*   bucket_gains [B*k] (caller sizes them with orc_num_buckets)            */
+/*   chosen: -1 when the best bucket wins, else the winning partition p     */
+/*   seeds/gains [k], nseeds, coverage: the final solution                  */
+/* ------------------------------------------------------------------------ */
+int orc_randgreedi(int64_t n, int64_t theta, const int64_t *set_off, const int32_t *members,
+                   const int64_t *vtx_off, const int32_t *set_ids, int32_t k, int32_t P,
+                   uint64_t pseed, int32_t trunc, double delta,
+                   int32_t *local_seeds, int64_t *local_gains, int32_t *local_n,
+                   int64_t *local_cov, int64_t *thr, int64_t *bucket_cov, int32_t *bucket_n,
+                   int32_t *bucket_seeds, int64_t *bucket_gains, int32_t *chosen,
+                   int32_t *seeds, int64_t *gains, int32_t *nseeds, int64_t *coverage) {
+    int32_t *part = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *allowed = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *stream = (int32_t *)malloc((size_t)P * (size_t)k * sizeof(int32_t));
+    if (!part || !allowed || !stream) { free(part); free(allowed); free(stream); return -1; }
+    orc_partition(n, P, pseed, part);
+
+    /* local greedy on every partition V_p, all k seeds */
+    for (int32_t p = 0; p < P; ++p) {
+        int64_t nc = 0;
+        for (int64_t v = 0; v < n; ++v) if (part[v] == p) allowed[nc++] = (int32_t)v;
+        if (orc_greedy(n, theta, set_off, members, vtx_off, set_ids, k, allowed, nc,
+                       local_seeds + (int64_t)p * k, local_gains + (int64_t)p * k,
+                       &local_n[p], &local_cov[p])) {
+            free(part); free(allowed); free(stream); return -1;
+        }
+    }
+
+    /* stream order: local rank j first, then partition p */
+    int64_t ns = 0;
+    for (int32_t j = 0; j < trunc && j < k; ++j)
+        for (int32_t p = 0; p < P; ++p)
+            if (j < local_n[p]) stream[ns++] = local_seeds[(int64_t)p * k + j];
+
+    /* l = largest single covering subset; u = k l */
+    int64_t l = 0;
+    for (int64_t v = 0; v < n; ++v)
+        if (vtx_off[v + 1] - vtx_off[v] > l) l = vtx_off[v + 1] - vtx_off[v];
+    int32_t B = orc_num_buckets(k, delta);
+    orc_bucket_thresholds(l, k, delta, B, thr);
+    if (orc_stream_buckets(theta, vtx_off, set_ids, stream, ns, k, B, thr, bucket_cov,
+                           bucket_n, bucket_seeds, bucket_gains)) {
+        free(part); free(allowed); free(stream); return -1;
+    }
+
+    /* best bucket (ties: smallest b) vs best local solution (ties: smallest p) */
+    int32_t bstar = 0;
+    for (int32_t b = 1; b < B; ++b) if (bucket_cov[b] > bucket_cov[bstar]) bstar = b;
+    int32_t pbest = 0;
+    for (int32_t p = 1; p < P; ++p) if (local_cov[p] > local_cov[pbest]) pbest = p;
+    if (bucket_cov[bstar] >= local_cov[pbest]) {
+        *chosen = -1;
+        *nseeds = bucket_n[bstar];
+        *coverage = bucket_cov[bstar];
+        for (int32_t j = 0; j < bucket_n[bstar]; ++j) {
+            seeds[j] = bucket_seeds[(int64_t)bstar * k + j];
+            gains[j] = bucket_gains[(int64_t)bstar * k + j];
+        }
+    } else {
+        *chosen = pbest;
+        *nseeds = local_n[pbest];
+        *coverage = local_cov[pbest];
+        for (int32_t j = 0; j < local_n[pbest]; ++j) {
+            seeds[j] = local_seeds[(int64_t)pbest * k + j];
+            gains[j] = local_gains[(int64_t)pbest * k + j];
+        }
+    }
+    free(part); free(allowed); free(stream);
+    return 0;
+}
