@@ -1,0 +1,176 @@
+/* im.h -- C ABI of libim, the GB300 (sm_103a) RIS influence-maximization hot path.
+ *
+ * The method is GreediRIS (arXiv 2408.10982): sample random reverse-reachable
+ * (RRR) sets (Def. 3, Sec. 2.1 "Sample"), turn them into covering subsets
+ * S(v) = { i : v in R(i) } (Sec. 3.2), and select k seeds by max-k-cover,
+ * either with the standard greedy (Sec. 3.2) or with RandGreedi over a random
+ * vertex partition (Alg. 3, Alg. 4) whose local solutions are merged by the
+ * streaming threshold algorithm (Alg. 5), optionally truncated (Sec. 3.3.2).
+ * On one GPU the paper's m machines become m vertex partitions processed by
+ * separate thread blocks, and its message passing becomes device memory.
+ *
+ * Conventions for every call:
+ *  - Returns an im_status; IM_OK is 0, errors are negative.  No C++
+ *    exception crosses this boundary.  im_last_error() gives the text of the
+ *    calling thread's last failure.
+ *  - Array arguments are plain pointers to either host or device memory; the
+ *    library tells them apart with cudaPointerGetAttributes.  Input arrays
+ *    are read during the call (and copied if kept).  Output arrays are
+ *    written; when an output is in host memory the call synchronises its
+ *    stream before returning, when all outputs are device memory the call
+ *    only enqueues work on the stream (outputs valid once the stream reaches
+ *    that point).
+ *  - The caller owns every array it passes.  The library owns the opaque
+ *    handles (im_graph, im_pool) and all device memory behind them; handles
+ *    live on the device that was current when they were created.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - Vertex ids are int32 in [0, n); edge and entry counts are int64; sample
+ *    ids are uint64 below 2^32.
+ *  - Randomness is Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit
+ *    seed, with one counter per (sample, edge group), (sample, vertex) or
+ *    (vertex) and a domain tag in counter word 3; results are therefore
+ *    bit-identical for any launch shape and any split of sample ids.
+ */
+#ifndef IM_H
+#define IM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IM_OK = 0,
+    IM_ERR_INVALID_ARG = -1,   /* a size, id, pointer or option is out of range */
+    IM_ERR_OOM = -2,           /* device memory could not be allocated */
+    IM_ERR_CUDA = -3,          /* a CUDA runtime call failed (text in im_last_error) */
+    IM_ERR_TIMEOUT = -4,       /* a bounded device wait expired (grid barrier, stream flag) */
+    IM_ERR_CAPACITY = -5,      /* a pool or queue capacity was exceeded; state unchanged */
+    IM_ERR_BUSY = -6,          /* the request is still running (serving poll) */
+    IM_ERR_UNSUPPORTED = -7    /* a valid request this build cannot run (e.g. no GPU) */
+} im_status;
+
+typedef enum { IM_IC = 0, IM_LT = 1 } im_model;
+
+typedef enum { IM_GREEDY_PLAIN = 0, IM_RANDGREEDI = 1 } im_cover_algo;
+
+/* Options of im_max_k_cover.
+ *   algo            IM_GREEDY_PLAIN: standard greedy over all of V (Sec. 3.2).
+ *                   IM_RANDGREEDI: Alg. 4 with Alg. 5 aggregation.
+ *   partitions      number of random vertex parts m (RandGreedi), 1..4096.
+ *   alpha_num/den   truncation alpha = num/den in (0, 1]: every partition
+ *                   computes k local seeds and streams its first
+ *                   max(1, ceil(alpha k)) of them (Sec. 3.3.2).
+ *   delta           bucket spacing of the streaming algorithm, 0 < delta < 1/2
+ *                   (Alg. 5); B = least b >= 1 with (1+delta)^b >= k buckets.
+ *   partition_seed  Philox key of the vertex partition (Alg. 3).
+ *   fused           RandGreedi only: 1 runs local greedy and aggregation in
+ *                   one cooperative launch with the aggregator consuming seeds
+ *                   as they are produced (streaming overlap); 0 runs them as
+ *                   two launches.  Results are identical. */
+typedef struct {
+    int32_t algo;
+    int32_t partitions;
+    int32_t alpha_num;
+    int32_t alpha_den;
+    double delta;
+    uint64_t partition_seed;
+    int32_t fused;
+    int32_t reserved;
+} im_cover_opts;
+
+typedef struct im_graph im_graph;   /* device-resident graph, library-owned */
+typedef struct im_pool im_pool;     /* device-resident RRR pool, append-only */
+
+/* Text of a status code / of this thread's last failure (never NULL). */
+const char *im_status_str(im_status s);
+const char *im_last_error(void);
+
+/* Library and device facts: number of SMs, device ordinal in use. */
+im_status im_device_info(int32_t *num_sms, int32_t *device);
+
+/* ---- graph (Sec. 3.4 S1: the whole graph is replicated on every machine) --
+ * in_off  int64[n+1]  in-CSR offsets (non-decreasing, in_off[0] = 0, in_off[n] = m)
+ * in_src  int32[m]    source vertex of each in-edge; edges of a vertex in any
+ *                     fixed order -- the edge id e is the CSR position
+ * w       uint32[m]   edge weight as a 32-bit threshold: for IC, edge e is live
+ *                     in sample s iff its Philox coin < w[e]; for LT, w[e] is
+ *                     the probability (x 2^32) that the head picks this in-edge,
+ *                     and a vertex's weights must sum to at most 2^32.
+ * Copies the arrays to the device.  Validates offsets and ids
+ * (IM_ERR_INVALID_ARG).  n >= 1, 0 <= m < 2^31. */
+im_status im_graph_create(const int64_t *in_off, const int32_t *in_src, const uint32_t *w,
+                          int64_t n, int64_t m, void *stream, im_graph **out);
+im_status im_graph_destroy(im_graph *g);
+/* n, m of a graph; lt_valid = 1 if every vertex's weights sum to <= 2^32. */
+im_status im_graph_info(const im_graph *g, int64_t *n, int64_t *m, int32_t *lt_valid);
+
+/* ---- RRR pool ---------------------------------------------------------------
+ * Holds up to max_sets RRR sets with up to max_entries members in total, as
+ * CSR by position (set_off int64[theta+1], members int32[T], each set
+ * ascending), plus the covering-subset index built from it.  Pools are
+ * append-only (samples of later IMM rounds extend earlier ones, Sec. 3.2). */
+im_status im_pool_create(const im_graph *g, int64_t max_sets, int64_t max_entries,
+                         im_pool **out);
+im_status im_pool_destroy(im_pool *p);
+/* Drop every set (theta = 0) without freeing memory. */
+im_status im_pool_reset(im_pool *p);
+/* theta, total entries T, and the edges examined by all sampling so far
+ * (IC: every in-edge of every member; LT: in-edges up to and including the
+ * picked one, or all in-edges when none is picked). */
+im_status im_pool_info(const im_pool *p, int64_t *theta, int64_t *total, int64_t *examined);
+
+/* ---- Sample (Alg. 1 "Sample"; Def. 3; Sec. 2.1) ------------------------------
+ * Appends the RRR sets of sample ids first_sample_id .. first_sample_id +
+ * num_samples - 1 to the pool, in id order.  Sample s draws its root
+ * uniformly from V and runs a stochastic reverse BFS (IC) or the backward
+ * random walk of the LT live-edge world (LT, requires lt_valid).
+ * IM_ERR_CAPACITY if the pool would overflow (pool unchanged).
+ * Synchronises the stream (the new totals are read back). */
+im_status im_sample_rrr(const im_graph *g, im_model model, uint64_t seed,
+                        uint64_t first_sample_id, uint64_t num_samples, im_pool *pool,
+                        void *stream);
+
+/* Copy the pool's CSR out: set_off int64[theta+1], members int32[T]. */
+im_status im_pool_export(const im_pool *p, int64_t *set_off, int32_t *members, void *stream);
+
+/* Build the covering subsets S(v) (Sec. 3.2; the all-to-all of Alg. 3 gathers
+ * exactly these rows).  Done implicitly by im_max_k_cover when stale. */
+im_status im_pool_index(im_pool *p, void *stream);
+/* Copy S(v) out: vtx_off int64[n+1], set_ids int32[T].  The order of set ids
+ * within one S(v) is unspecified (the cover does not depend on it). */
+im_status im_index_export(const im_pool *p, int64_t *vtx_off, int32_t *set_ids, void *stream);
+
+/* ---- SelectSeeds: max-k-cover over the pool (Sec. 3.2, Alg. 4, Alg. 5) -------
+ * Universe: the pool's theta sets.  Greedy ties go to the smallest vertex id;
+ * a greedy stops early when every remaining gain is zero, so num_seeds may be
+ * < k.  Outputs: seeds int32[k], gains int64[k] (marginal gain of each seed
+ * when it was taken; for a winning bucket, its gain on entering the bucket),
+ * num_seeds, coverage = |union of S(seed)|.  k >= 1.
+ * IM_ERR_TIMEOUT if a bounded device wait expired. */
+im_status im_max_k_cover(im_pool *p, int32_t k, const im_cover_opts *opts, int32_t *seeds,
+                         int64_t *gains, int32_t *num_seeds, int64_t *coverage, void *stream);
+
+/* Details of the pool's last IM_RANDGREEDI cover, for parity checks:
+ *   local_seeds int32[P*k], local_gains int64[P*k], local_n int32[P],
+ *   local_cov int64[P]                       -- Alg. 4 local solutions
+ *   thr int64[B], bucket_cov int64[B], bucket_n int32[B],
+ *   bucket_seeds int32[B*k], bucket_gains int64[B*k]   -- Alg. 5 buckets
+ *   chosen: -1 if the best bucket won, else the winning partition.
+ * Any pointer may be NULL.  *P_out and *B_out receive P and B. */
+im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out,
+                                int32_t *local_seeds, int64_t *local_gains, int32_t *local_n,
+                                int64_t *local_cov, int64_t *thr, int64_t *bucket_cov,
+                                int32_t *bucket_n, int32_t *bucket_seeds, int64_t *bucket_gains,
+                                int32_t *chosen, void *stream);
+
+/* Vertex partition of Alg. 3: part[v] = (Philox(v,0,0,4).x * P) >> 32. */
+im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
+                       void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IM_H */

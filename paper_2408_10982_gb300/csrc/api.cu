@@ -1,0 +1,478 @@
+// api.cu -- the extern "C" entry points of libim (declared in include/im.h).
+//
+// Each entry point validates its arguments, runs the kernels of sample.cu,
+// index.cu and cover.cu on the caller's stream, and maps device status words
+// and CUDA errors to im_status.  No C++ exception crosses the boundary.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace im {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+im_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? IM_ERR_OOM : IM_ERR_CUDA;
+}
+
+im_status map_dev_status(int code, const char *where) {
+    switch (code) {
+        case kDevOk: return IM_OK;
+        case kDevTimeout:
+            set_error(std::string(where) + ": a bounded device wait expired");
+            return IM_ERR_TIMEOUT;
+        case kDevQueueOverflow:
+        case kDevStageOverflow:
+            set_error(std::string(where) + ": capacity exceeded");
+            return IM_ERR_CAPACITY;
+        case kDevBadInput:
+            set_error(std::string(where) + ": invalid input");
+            return IM_ERR_INVALID_ARG;
+        default:
+            set_error(std::string(where) + ": unknown device status");
+            return IM_ERR_CUDA;
+    }
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+im_status pool_scratch(im_pool *p, size_t bytes, void **out) {
+    if (bytes > p->scratch_bytes) {
+        if (p->scratch) {
+            IM_CUDA(cudaDeviceSynchronize());
+            cudaFree(p->scratch);
+            p->scratch = nullptr;
+            p->scratch_bytes = 0;
+        }
+        size_t want = bytes + bytes / 4 + 4096;
+        IM_CUDA(cudaMalloc(&p->scratch, want));
+        p->scratch_bytes = want;
+    }
+    *out = p->scratch;
+    return IM_OK;
+}
+
+namespace {
+
+bool is_device_ptr(const void *ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+__global__ void k_validate_graph(const int64_t *in_off, const int32_t *in_src, int64_t n,
+                                 int64_t m, int *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (in_off[v + 1] < in_off[v]) atomicExch(bad, 1);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t u = in_src[e];
+        if (u < 0 || (int64_t)u >= n) atomicExch(bad, 2);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (in_off[0] != 0 || in_off[n] != m))
+        atomicExch(bad, 3);
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// copy to a caller buffer (host or device); returns whether it was host memory
+im_status copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st, bool *host) {
+    if (!dst || bytes == 0) return IM_OK;
+    if (!is_device_ptr(dst)) *host = true;
+    IM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return IM_OK;
+}
+
+im_status pool_results(im_pool *p, size_t bytes, void **out) {
+    if (bytes > p->res_bytes) {
+        if (p->res) {
+            IM_CUDA(cudaDeviceSynchronize());
+            cudaFree(p->res);
+            p->res = nullptr;
+            p->res_bytes = 0;
+        }
+        IM_CUDA(cudaMalloc(&p->res, bytes));
+        p->res_bytes = bytes;
+    }
+    *out = p->res;
+    return IM_OK;
+}
+
+#define IM_TRY(expr)                   \
+    do {                               \
+        im_status _s = (expr);         \
+        if (_s != IM_OK) return _s;    \
+    } while (0)
+
+}  // namespace
+}  // namespace im
+
+using namespace im;
+
+extern "C" {
+
+const char *im_status_str(im_status s) {
+    switch (s) {
+        case IM_OK: return "ok";
+        case IM_ERR_INVALID_ARG: return "invalid argument";
+        case IM_ERR_OOM: return "out of device memory";
+        case IM_ERR_CUDA: return "CUDA error";
+        case IM_ERR_TIMEOUT: return "bounded device wait expired";
+        case IM_ERR_CAPACITY: return "capacity exceeded";
+        case IM_ERR_BUSY: return "busy";
+        case IM_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *im_last_error(void) { return g_last_error.c_str(); }
+
+im_status im_device_info(int32_t *sms, int32_t *device) {
+    int dev = 0, count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        set_error("no CUDA device");
+        return IM_ERR_UNSUPPORTED;
+    }
+    IM_CUDA(cudaGetDevice(&dev));
+    if (sms) *sms = num_sms();
+    if (device) *device = dev;
+    return IM_OK;
+}
+
+im_status im_graph_create(const int64_t *in_off, const int32_t *in_src, const uint32_t *w,
+                          int64_t n, int64_t m, void *stream, im_graph **out) {
+    if (!out || !in_off || n < 1 || n > INT32_MAX || m < 0 || m >= ((int64_t)1 << 31) ||
+        (m > 0 && (!in_src || !w))) {
+        set_error("im_graph_create: bad sizes or null pointers");
+        return IM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    cudaStream_t st = as_stream(stream);
+    im_graph *g = new (std::nothrow) im_graph();
+    if (!g) return IM_ERR_OOM;
+    std::memset(g, 0, sizeof(*g));
+    cudaGetDevice(&g->device);
+    g->n = n;
+    g->m = m;
+    const int64_t mpad = (m + 3) & ~(int64_t)3;   // 16-byte groups of four edges
+    auto fail = [&](im_status s) {
+        cudaFree(g->in_off);
+        cudaFree(g->in_src);
+        cudaFree(g->w);
+        delete g;
+        return s;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&g->in_off, (size_t)(n + 1) * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&g->in_src, (size_t)std::max<int64_t>(mpad, 4) * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&g->w, (size_t)std::max<int64_t>(mpad, 4) * 4)) != cudaSuccess)
+        return fail(cuda_fail(e, "im_graph_create: cudaMalloc"));
+    if ((e = cudaMemcpyAsync(g->in_off, in_off, (size_t)(n + 1) * 8, cudaMemcpyDefault, st)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(g->in_src, 0, (size_t)std::max<int64_t>(mpad, 4) * 4, st)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(g->w, 0, (size_t)std::max<int64_t>(mpad, 4) * 4, st)) != cudaSuccess)
+        return fail(cuda_fail(e, "im_graph_create: copy"));
+    if (m > 0 &&
+        ((e = cudaMemcpyAsync(g->in_src, in_src, (size_t)m * 4, cudaMemcpyDefault, st)) !=
+             cudaSuccess ||
+         (e = cudaMemcpyAsync(g->w, w, (size_t)m * 4, cudaMemcpyDefault, st)) != cudaSuccess))
+        return fail(cuda_fail(e, "im_graph_create: copy"));
+    int *d_bad = nullptr;
+    if ((e = cudaMallocAsync((void **)&d_bad, sizeof(int), st)) != cudaSuccess)
+        return fail(cuda_fail(e, "im_graph_create: cudaMallocAsync"));
+    cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+    k_validate_graph<<<num_sms() * 4, 256, 0, st>>>(g->in_off, g->in_src, n, m, d_bad);
+    int bad = 0;
+    cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d_bad, st);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(cuda_fail(e, "im_graph_create: validation"));
+    if (bad) {
+        set_error(bad == 2 ? "im_graph_create: source id out of range"
+                           : "im_graph_create: offsets not a valid CSR of m edges");
+        return fail(IM_ERR_INVALID_ARG);
+    }
+    g->lt_valid = -1;   // unknown until the LT weights are summed
+    *out = g;
+    return IM_OK;
+}
+
+im_status im_graph_destroy(im_graph *g) {
+    if (!g) return IM_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaFree(g->in_off);
+    cudaFree(g->in_src);
+    cudaFree(g->w);
+    cudaFree(g->lt_cdf);
+    delete g;
+    return IM_OK;
+}
+
+im_status im_graph_info(const im_graph *g, int64_t *n, int64_t *m, int32_t *lt_valid) {
+    if (!g) return IM_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (lt_valid) {
+        if (!g->lt_cdf) IM_TRY(build_lt_cdf(const_cast<im_graph *>(g), 0));
+        *lt_valid = g->lt_valid;
+    }
+    return IM_OK;
+}
+
+im_status im_pool_create(const im_graph *g, int64_t max_sets, int64_t max_entries,
+                         im_pool **out) {
+    if (!g || !out || max_sets < 0 || max_entries < 0 || max_sets >= ((int64_t)1 << 31)) {
+        set_error("im_pool_create: bad arguments");
+        return IM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(g->device);
+    *out = nullptr;
+    im_pool *p = new (std::nothrow) im_pool();
+    if (!p) return IM_ERR_OOM;
+    std::memset(p, 0, sizeof(*p));
+    p->g = g;
+    p->device = g->device;
+    p->max_sets = max_sets;
+    p->max_entries = max_entries;
+    const int64_t n = g->n;
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->set_off, (size_t)(max_sets + 1) * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&p->members, (size_t)std::max<int64_t>(max_entries, 1) * 4)) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&p->vtx_off, (size_t)(n + 1) * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&p->set_ids, (size_t)std::max<int64_t>(max_entries, 1) * 4)) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&p->vtx_cursor, (size_t)n * 4)) != cudaSuccess) {
+        im_status s = cuda_fail(e, "im_pool_create: cudaMalloc");
+        im_pool_destroy(p);
+        return s;
+    }
+    cudaMemset(p->set_off, 0, 8);
+    cudaMemset(p->vtx_off, 0, (size_t)(n + 1) * 8);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        im_status s = cuda_fail(e, "im_pool_create");
+        im_pool_destroy(p);
+        return s;
+    }
+    *out = p;
+    return IM_OK;
+}
+
+im_status im_pool_destroy(im_pool *p) {
+    if (!p) return IM_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    cudaFree(p->set_off);
+    cudaFree(p->members);
+    cudaFree(p->vtx_off);
+    cudaFree(p->set_ids);
+    cudaFree(p->vtx_cursor);
+    cudaFree(p->pkeys);
+    cudaFree(p->part);
+    cudaFree(p->part_off);
+    cudaFree(p->part_vtx);
+    cudaFree(p->part_loc);
+    cudaFree(p->rg_block);
+    cudaFree(p->scratch);
+    cudaFree(p->res);
+    delete p;
+    return IM_OK;
+}
+
+im_status im_pool_reset(im_pool *p) {
+    if (!p) return IM_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    p->theta = p->total = p->examined = 0;
+    p->index_valid = false;
+    p->pkeys_valid = false;
+    IM_CUDA(cudaMemset(p->set_off, 0, 8));
+    return IM_OK;
+}
+
+im_status im_pool_info(const im_pool *p, int64_t *theta, int64_t *total, int64_t *examined) {
+    if (!p) return IM_ERR_INVALID_ARG;
+    if (theta) *theta = p->theta;
+    if (total) *total = p->total;
+    if (examined) *examined = p->examined;
+    return IM_OK;
+}
+
+im_status im_sample_rrr(const im_graph *g, im_model model, uint64_t seed,
+                        uint64_t first_sample_id, uint64_t num_samples, im_pool *pool,
+                        void *stream) {
+    if (!g || !pool || pool->g != g || (model != IM_IC && model != IM_LT) ||
+        first_sample_id + num_samples > ((uint64_t)1 << 32) || num_samples >= ((uint64_t)1 << 31)) {
+        set_error("im_sample_rrr: bad arguments (graph/pool mismatch, model or sample ids)");
+        return IM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(g->device);
+    return sample_append(g, model, seed, first_sample_id, num_samples, pool, as_stream(stream));
+}
+
+im_status im_pool_export(const im_pool *p, int64_t *set_off, int32_t *members, void *stream) {
+    if (!p) return IM_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    cudaStream_t st = as_stream(stream);
+    bool host = false;
+    IM_TRY(copy_out(set_off, p->set_off, (size_t)(p->theta + 1) * 8, st, &host));
+    IM_TRY(copy_out(members, p->members, (size_t)p->total * 4, st, &host));
+    if (host) IM_CUDA(cudaStreamSynchronize(st));
+    return IM_OK;
+}
+
+im_status im_pool_index(im_pool *p, void *stream) {
+    if (!p) return IM_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    return build_index(p, as_stream(stream));
+}
+
+im_status im_index_export(const im_pool *pc, int64_t *vtx_off, int32_t *set_ids, void *stream) {
+    if (!pc) return IM_ERR_INVALID_ARG;
+    im_pool *p = const_cast<im_pool *>(pc);
+    DeviceGuard dg(p->device);
+    cudaStream_t st = as_stream(stream);
+    IM_TRY(build_index(p, st));
+    bool host = false;
+    IM_TRY(copy_out(vtx_off, p->vtx_off, (size_t)(p->g->n + 1) * 8, st, &host));
+    IM_TRY(copy_out(set_ids, p->set_ids, (size_t)p->total * 4, st, &host));
+    if (host) IM_CUDA(cudaStreamSynchronize(st));
+    return IM_OK;
+}
+
+im_status im_max_k_cover(im_pool *p, int32_t k, const im_cover_opts *opts, int32_t *seeds,
+                         int64_t *gains, int32_t *num_seeds, int64_t *coverage, void *stream) {
+    if (!p || k < 1 || k > (1 << 24)) {
+        set_error("im_max_k_cover: bad arguments");
+        return IM_ERR_INVALID_ARG;
+    }
+    im_cover_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.algo = IM_GREEDY_PLAIN;
+    if (opts) o = *opts;
+    if (o.algo == IM_RANDGREEDI) {
+        if (o.partitions < 1 || o.partitions > 4096 || o.alpha_num < 1 || o.alpha_den < 1 ||
+            o.alpha_num > o.alpha_den || !(o.delta > 0.0 && o.delta < 0.5)) {
+            set_error("im_max_k_cover: RandGreedi options out of range");
+            return IM_ERR_INVALID_ARG;
+        }
+    } else if (o.algo != IM_GREEDY_PLAIN) {
+        set_error("im_max_k_cover: unknown algorithm");
+        return IM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(p->device);
+    cudaStream_t st = as_stream(stream);
+    IM_TRY(build_index(p, st));
+    // results: seeds[k] gains[k] nseeds cov status
+    const size_t o_seeds = 0, o_gains = ((size_t)k * 4 + 255) & ~(size_t)255;
+    const size_t o_tail = o_gains + (((size_t)k * 8 + 255) & ~(size_t)255);
+    void *res = nullptr;
+    IM_TRY(pool_results(p, o_tail + 64, &res));
+    char *R = (char *)res;
+    int32_t *d_seeds = (int32_t *)(R + o_seeds);
+    int64_t *d_gains = (int64_t *)(R + o_gains);
+    int64_t *d_cov = (int64_t *)(R + o_tail);
+    int32_t *d_nseeds = (int32_t *)(R + o_tail + 8);
+    int *d_status = (int *)(R + o_tail + 16);
+    IM_CUDA(cudaMemsetAsync(R + o_tail, 0, 64, st));
+    im_status s = o.algo == IM_RANDGREEDI
+                      ? randgreedi(p, k, &o, d_seeds, d_gains, d_nseeds, d_cov, st, d_status)
+                      : greedy_plain(p, k, d_seeds, d_gains, d_nseeds, d_cov, st, d_status);
+    if (s != IM_OK) return s;
+    int32_t hdr[6];
+    IM_CUDA(cudaMemcpyAsync(hdr, R + o_tail, sizeof(hdr), cudaMemcpyDeviceToHost, st));
+    IM_CUDA(cudaStreamSynchronize(st));
+    if (hdr[4] != kDevOk) return map_dev_status(hdr[4], "im_max_k_cover");
+    const int32_t ns = hdr[2];
+    bool host = false;
+    IM_TRY(copy_out(seeds, d_seeds, (size_t)ns * 4, st, &host));
+    IM_TRY(copy_out(gains, d_gains, (size_t)ns * 8, st, &host));
+    IM_TRY(copy_out(num_seeds, d_nseeds, 4, st, &host));
+    IM_TRY(copy_out(coverage, d_cov, 8, st, &host));
+    if (host) IM_CUDA(cudaStreamSynchronize(st));
+    return IM_OK;
+}
+
+im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out,
+                                int32_t *local_seeds, int64_t *local_gains, int32_t *local_n,
+                                int64_t *local_cov, int64_t *thr, int64_t *bucket_cov,
+                                int32_t *bucket_n, int32_t *bucket_seeds, int64_t *bucket_gains,
+                                int32_t *chosen, void *stream) {
+    if (!p || p->rg_P == 0) {
+        set_error("im_randgreedi_details: no RandGreedi run on this pool");
+        return IM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(p->device);
+    cudaStream_t st = as_stream(stream);
+    const size_t P = p->rg_P, B = p->rg_B, k = p->rg_k;
+    if (P_out) *P_out = (int32_t)P;
+    if (B_out) *B_out = (int32_t)B;
+    if (chosen) *chosen = p->rg_chosen;
+    bool host = false;
+    IM_TRY(copy_out(local_seeds, p->rg_local_seeds, P * k * 4, st, &host));
+    IM_TRY(copy_out(local_gains, p->rg_local_gains, P * k * 8, st, &host));
+    IM_TRY(copy_out(local_n, p->rg_local_n, P * 4, st, &host));
+    IM_TRY(copy_out(local_cov, p->rg_local_cov, P * 8, st, &host));
+    IM_TRY(copy_out(thr, p->rg_thr, B * 8, st, &host));
+    IM_TRY(copy_out(bucket_cov, p->rg_bucket_cov, B * 8, st, &host));
+    IM_TRY(copy_out(bucket_n, p->rg_bucket_n, B * 4, st, &host));
+    IM_TRY(copy_out(bucket_seeds, p->rg_bucket_seeds, B * k * 4, st, &host));
+    IM_TRY(copy_out(bucket_gains, p->rg_bucket_gains, B * k * 8, st, &host));
+    if (host) IM_CUDA(cudaStreamSynchronize(st));
+    return IM_OK;
+}
+
+im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
+                       void *stream) {
+    if (n < 1 || n > INT32_MAX || P < 1 || !part) return IM_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    const bool dev = is_device_ptr(part);
+    int32_t *d = part;
+    if (!dev) IM_CUDA(cudaMallocAsync((void **)&d, (size_t)n * 4, st));
+    IM_TRY(launch_partition_labels(n, P, partition_seed, d, st));
+    if (!dev) {
+        IM_CUDA(cudaMemcpyAsync(part, d, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+        IM_CUDA(cudaFreeAsync(d, st));
+        IM_CUDA(cudaStreamSynchronize(st));
+    }
+    return IM_OK;
+}
+
+}  // extern "C"

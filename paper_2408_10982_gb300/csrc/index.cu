@@ -1,0 +1,249 @@
+// index.cu -- covering subsets S(v) (Sec. 3.2) and the RandGreedi partition
+// structures (Alg. 3).
+//
+// S(v) is the transpose of the RRR CSR: a histogram of member ids, an
+// exclusive scan into vtx_off, and a scatter of set ids.  On one GPU this is
+// the paper's all-to-all shuffle of covering subsets (Alg. 3), done in place.
+// Set ids inside one S(v) land in atomic order; nothing downstream depends on
+// that order.
+//
+// For RandGreedi every vertex gets a Philox label part(v) in [0, P) and a
+// local index loc(v) = its rank among the vertices of its part (ascending id).
+// Each RRR set's members are then re-keyed as (part << 32 | loc) and sorted,
+// so that R(i) restricted to V_p is one contiguous run found by binary search.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace im {
+
+namespace {
+
+constexpr int kChunk = 4096;   // vertices per chunk of the stable partition scatter
+
+// Each warp takes 32 consecutive sets and spreads their members over lanes.
+template <typename F>
+__device__ __forceinline__ void for_each_entry_of_32_sets(const int64_t *set_off, int64_t i0,
+                                                          int64_t theta, int lane, F &&f) {
+    const int64_t i = i0 + lane;
+    int64_t o = 0, len = 0;
+    if (i < theta) {
+        o = set_off[i];
+        len = set_off[i + 1] - o;
+    }
+    const int64_t incl = warp_incl_scan<int64_t>(len, lane);
+    const int64_t total = __shfl_sync(kFull, incl, 31);
+    for (int64_t base = 0; base < total; base += 32) {
+        const int64_t t = base + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
+            if (c <= t) owner += step;
+        }
+        const int64_t o_incl = __shfl_sync(kFull, incl, owner);
+        const int64_t o_len = __shfl_sync(kFull, len, owner);
+        const int64_t o_off = __shfl_sync(kFull, o, owner);
+        if (t < total) f(i0 + owner, o_off + (t - (o_incl - o_len)));
+    }
+}
+
+__global__ void k_vertex_hist(const int32_t *members, int64_t T, int32_t *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < T;
+         base += stride) {
+        const int64_t t = base + lane;
+        const int32_t u = t < T ? members[t] : -1 - lane;   // distinct dummies
+        const unsigned peers = __match_any_sync(kFull, u);
+        if (u >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[u], __popc(peers));
+    }
+}
+
+__global__ void k_scatter(const int64_t *set_off, const int32_t *members, int64_t theta,
+                          const int64_t *vtx_off, int32_t *cursor, int32_t *set_ids) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+         i0 < theta; i0 += warps * 32) {
+        for_each_entry_of_32_sets(set_off, i0, theta, lane, [&](int64_t i, int64_t t) {
+            const int32_t u = members[t];
+            const int64_t pos = vtx_off[u] + atomicAdd(&cursor[u], 1);
+            set_ids[pos] = (int32_t)i;
+        });
+    }
+}
+
+__global__ void k_part_labels(int64_t n, uint32_t P, uint64_t pseed, int32_t *part) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        part[v] = vertex_part(pseed, (uint32_t)v, P);
+}
+
+// hist[c * P + p] = |{v in chunk c : part(v) = p}|
+__global__ void k_part_hist(const int32_t *part, int64_t n, int32_t P, int32_t *hist) {
+    extern __shared__ int32_t sh[];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) sh[p] = 0;
+    __syncthreads();
+    const int64_t v0 = (int64_t)blockIdx.x * kChunk;
+    const int64_t v1 = min(n, v0 + kChunk);
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) atomicAdd(&sh[part[v]], 1);
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x) hist[(int64_t)blockIdx.x * P + p] = sh[p];
+}
+
+// part_off[p] = vertices in parts < p; hist turns into chunk start offsets
+__global__ void k_part_offsets(int32_t *hist, int64_t nchunks, int32_t P, int32_t *part_off) {
+    // one thread per part scans its column; then a serial scan of the totals
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        int32_t run = 0;
+        for (int64_t c = 0; c < nchunks; ++c) {
+            const int32_t h = hist[c * P + p];
+            hist[c * P + p] = run;
+            run += h;
+        }
+        part_off[p + 1] = run;   // temporarily the size of part p
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        part_off[0] = 0;
+        for (int p = 0; p < P; ++p) {
+            const int32_t sz = part_off[p + 1];
+            part_off[p + 1] = run + sz;
+            run += sz;
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x)
+        for (int64_t c = 0; c < nchunks; ++c) hist[c * P + p] += part_off[p];
+}
+
+// One warp per chunk writes its vertices in ascending order into their parts.
+__global__ void k_part_scatter(const int32_t *part, int64_t n, int32_t P, const int32_t *hist,
+                               const int32_t *part_off, int32_t *part_vtx, int32_t *part_loc) {
+    extern __shared__ int32_t run[];   // per-part write cursor of this chunk
+    const int lane = threadIdx.x;
+    for (int p = lane; p < P; p += 32) run[p] = hist[(int64_t)blockIdx.x * P + p];
+    __syncwarp();
+    const int64_t v0 = (int64_t)blockIdx.x * kChunk;
+    const int64_t v1 = min(n, v0 + kChunk);
+    for (int64_t base = v0; base < v1; base += 32) {
+        const int64_t v = base + lane;
+        const int32_t p = v < v1 ? part[v] : -1 - lane;
+        const unsigned peers = __match_any_sync(kFull, p);
+        const int rank = __popc(peers & ((1u << lane) - 1));
+        int32_t at = 0;
+        if (v < v1) at = run[p] + rank;
+        __syncwarp();
+        if (v < v1 && rank == __popc(peers) - 1) run[p] = at + 1;
+        __syncwarp();
+        if (v < v1) {
+            part_vtx[at] = (int32_t)v;
+            part_loc[v] = at - part_off[p];
+        }
+    }
+}
+
+__global__ void k_part_keys(const int32_t *members, int64_t T, const int32_t *part,
+                            const int32_t *part_loc, uint64_t *keys) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = members[t];
+        keys[t] = ((uint64_t)(uint32_t)part[u] << 32) | (uint32_t)part_loc[u];
+    }
+}
+
+__global__ void k_max_seg(const int64_t *off, int64_t n, unsigned long long *out) {
+    unsigned long long m = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long d = (unsigned long long)(off[v + 1] - off[v]);
+        m = d > m ? d : m;
+    }
+    m = warp_max_u64(m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+}  // namespace
+
+im_status max_segment_length(const int64_t *off, int64_t n, int64_t *d_out, cudaStream_t st) {
+    IM_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int64_t), st));
+    k_max_seg<<<num_sms() * 4, 256, 0, st>>>(off, n, (unsigned long long *)d_out);
+    IM_CUDA(cudaGetLastError());
+    return IM_OK;
+}
+
+im_status launch_partition_labels(int64_t n, int32_t P, uint64_t pseed, int32_t *part,
+                                  cudaStream_t st) {
+    k_part_labels<<<num_sms() * 4, 256, 0, st>>>(n, (uint32_t)P, pseed, part);
+    IM_CUDA(cudaGetLastError());
+    return IM_OK;
+}
+
+im_status build_index(im_pool *p, cudaStream_t st) {
+    if (p->index_valid) return IM_OK;
+    const int64_t n = p->g->n, T = p->total, theta = p->theta;
+    IM_CUDA(cudaMemsetAsync(p->vtx_cursor, 0, (size_t)n * sizeof(int32_t), st));
+    if (T > 0) {
+        k_vertex_hist<<<num_sms() * 8, 256, 0, st>>>(p->members, T, p->vtx_cursor);
+        IM_CUDA(cudaGetLastError());
+    }
+    void *tmp = nullptr;
+    im_status s = pool_scratch(p, scan_tmp_bytes(n), &tmp);
+    if (s != IM_OK) return s;
+    s = exclusive_scan_i32_to_i64(p->vtx_cursor, p->vtx_off, n, nullptr, tmp, scan_tmp_bytes(n),
+                                  st);
+    if (s != IM_OK) return s;
+    IM_CUDA(cudaMemsetAsync(p->vtx_cursor, 0, (size_t)n * sizeof(int32_t), st));
+    if (theta > 0) {
+        k_scatter<<<num_sms() * 8, 256, 0, st>>>(p->set_off, p->members, theta, p->vtx_off,
+                                                 p->vtx_cursor, p->set_ids);
+        IM_CUDA(cudaGetLastError());
+    }
+    p->index_valid = true;
+    return IM_OK;
+}
+
+im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st) {
+    if (p->pkeys_valid && p->pkeys_P == P && p->pkeys_seed == pseed) return IM_OK;
+    const int64_t n = p->g->n, T = p->total, theta = p->theta;
+    if (!p->part) {
+        IM_CUDA(cudaMalloc(&p->part, (size_t)n * 4));
+        IM_CUDA(cudaMalloc(&p->part_vtx, (size_t)n * 4));
+        IM_CUDA(cudaMalloc(&p->part_loc, (size_t)n * 4));
+    }
+    if (p->part_cap < P) {
+        if (p->part_off) cudaFree(p->part_off);
+        IM_CUDA(cudaMalloc(&p->part_off, (size_t)(P + 1) * 4));
+        p->part_cap = P;
+    }
+    if (!p->pkeys) IM_CUDA(cudaMalloc(&p->pkeys, (size_t)std::max<int64_t>(1, p->max_entries) * 8));
+    im_status s = launch_partition_labels(n, P, pseed, p->part, st);
+    if (s != IM_OK) return s;
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    const size_t hist_bytes = (size_t)nchunks * P * 4;
+    const size_t sort_bytes = (size_t)(2 + 2 * std::max<int64_t>(theta, 1)) * 8;
+    void *tmp = nullptr;
+    s = pool_scratch(p, std::max(hist_bytes, sort_bytes), &tmp);
+    if (s != IM_OK) return s;
+    int32_t *hist = (int32_t *)tmp;
+    k_part_hist<<<(unsigned)nchunks, 256, (size_t)P * 4, st>>>(p->part, n, P, hist);
+    k_part_offsets<<<1, 256, 0, st>>>(hist, nchunks, P, p->part_off);
+    k_part_scatter<<<(unsigned)nchunks, 32, (size_t)P * 4, st>>>(p->part, n, P, hist,
+                                                                  p->part_off, p->part_vtx,
+                                                                  p->part_loc);
+    IM_CUDA(cudaGetLastError());
+    if (T > 0) {
+        k_part_keys<<<num_sms() * 8, 256, 0, st>>>(p->members, T, p->part, p->part_loc, p->pkeys);
+        IM_CUDA(cudaGetLastError());
+        s = segmented_sort<uint64_t>(p->pkeys, p->set_off, theta, tmp, sort_bytes, st);
+        if (s != IM_OK) return s;
+    }
+    p->pkeys_valid = true;
+    p->pkeys_P = P;
+    p->pkeys_seed = pseed;
+    return IM_OK;
+}
+
+}  // namespace im

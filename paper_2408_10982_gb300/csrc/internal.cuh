@@ -1,0 +1,259 @@
+// internal.cuh -- shared device helpers and handle layouts of libim (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/im.h"
+
+namespace im {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products of counter words 0 and 2 with the round constants,
+// xor-mixed with the other words and the key, key bumped by the Weyl pair.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a_lo = 0xD2511F53u * x.x, a_hi = __umulhi(0xD2511F53u, x.x);
+        const uint32_t b_lo = 0xCD9E8D57u * x.z, b_hi = __umulhi(0xCD9E8D57u, x.z);
+        x = make_uint4(b_hi ^ x.y ^ k0, b_lo, a_hi ^ x.w ^ k1, a_lo);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return x;
+}
+
+// Counter-word-3 domain tags: one independent stream per kind of draw.
+constexpr uint32_t kStreamRoot = 1;   // root of sample s: (s, 0, 0)
+constexpr uint32_t kStreamCoin = 2;   // IC coins of edges 4g..4g+3: (s, g lo, g hi)
+constexpr uint32_t kStreamPick = 3;   // LT in-edge pick of vertex v: (s, v, 0)
+constexpr uint32_t kStreamPart = 4;   // partition label of vertex v: (v, 0, 0)
+
+__device__ __forceinline__ uint32_t seed_lo(uint64_t seed) { return (uint32_t)seed; }
+__device__ __forceinline__ uint32_t seed_hi(uint64_t seed) { return (uint32_t)(seed >> 32); }
+
+// Uniform pick in [0, N) from a 32-bit draw: floor(r * N / 2^32).
+__device__ __forceinline__ uint32_t scale_u32(uint32_t r, uint32_t N) { return __umulhi(r, N); }
+
+__device__ __forceinline__ uint32_t rrr_root(uint64_t seed, uint32_t s, uint32_t n) {
+    return scale_u32(philox4x32_10(make_uint4(s, 0u, 0u, kStreamRoot), seed_lo(seed),
+                                   seed_hi(seed)).x, n);
+}
+
+__device__ __forceinline__ int32_t vertex_part(uint64_t pseed, uint32_t v, uint32_t P) {
+    return (int32_t)scale_u32(
+        philox4x32_10(make_uint4(v, 0u, 0u, kStreamPart), seed_lo(pseed), seed_hi(pseed)).x, P);
+}
+
+// ---------------------------------------------------------------------------
+// memory-model helpers and bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Device status codes written to a status word (mapped to im_status on the host).
+constexpr int kDevOk = 0;
+constexpr int kDevTimeout = 1;
+constexpr int kDevQueueOverflow = 2;
+constexpr int kDevStageOverflow = 3;
+constexpr int kDevBadInput = 4;
+
+__device__ __forceinline__ void raise_status(int *status, int code) { atomicCAS(status, 0, code); }
+
+// Segments longer than this many 64-bit keys are left unsorted by the
+// segmented sort (their readers scan them linearly).
+constexpr int kSortedKeyCap64 = 8192;
+
+// Every device spin-wait gives up after this many nanoseconds.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Software grid barrier for cooperative launches (all blocks co-resident).
+// Returns false (and raises kDevTimeout) if the other blocks did not arrive
+// within kWaitLimitNs; callers then leave the kernel.
+struct GridBarrier {
+    uint32_t count;
+    uint32_t gen;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, uint32_t nblocks, int *status) {
+    __shared__ int ok_flag;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint32_t g = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release_u32(&bar->gen, g + 1);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (ld_acquire_u32(&bar->gen) == g) {
+                if (global_ns() - t0 > kWaitLimitNs) {
+                    raise_status(status, kDevTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        // a block that sees an error raised elsewhere also stops
+        if (ok && *(volatile int *)status == kDevTimeout) ok = 0;
+        ok_flag = ok;
+    }
+    __syncthreads();
+    return ok_flag != 0;
+}
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(kFull, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+
+}  // namespace im
+
+// ---------------------------------------------------------------------------
+// handle layouts (host side)
+// ---------------------------------------------------------------------------
+struct im_graph {
+    int device;
+    int64_t n, m;
+    int64_t *in_off;     // [n+1]
+    int32_t *in_src;     // [m]
+    uint32_t *w;         // [m], 16-byte aligned
+    uint64_t *lt_cdf;    // [m] per-vertex inclusive running sums of w (LT), lazily built
+    int32_t lt_valid;
+    int64_t max_indeg;
+};
+
+struct im_pool {
+    const im_graph *g;
+    int device;
+    int64_t max_sets, max_entries;
+    int64_t theta, total, examined;   // host copies, valid after every call
+    int64_t *set_off;                 // [max_sets+1]
+    int32_t *members;                 // [max_entries]
+    // covering subsets
+    bool index_valid;
+    int64_t *vtx_off;                 // [n+1]
+    int32_t *set_ids;                 // [max_entries]; also the sampling stage
+    int32_t *vtx_cursor;              // [n] scratch
+    // RandGreedi partition-grouped member keys (part << 32 | local index)
+    uint64_t *pkeys;                  // [max_entries], lazily allocated
+    int32_t pkeys_P;                  // partition count / seed the keys were built for
+    uint64_t pkeys_seed;
+    bool pkeys_valid;
+    int32_t *part;                    // [n]
+    int32_t *part_off;                // [P+1]
+    int32_t *part_vtx;                // [n]
+    int32_t *part_loc;                // [n]
+    int32_t part_cap;                 // allocated P capacity of part_off
+    // last RandGreedi results (device)
+    int32_t rg_P, rg_B, rg_k, rg_chosen;
+    int32_t *rg_local_seeds;          // [P*k]
+    int64_t *rg_local_gains;          // [P*k]
+    int32_t *rg_local_n;              // [P]
+    int64_t *rg_local_cov;            // [P]
+    int64_t *rg_thr;                  // [B]
+    int64_t *rg_bucket_cov;           // [B]
+    int32_t *rg_bucket_n;             // [B]
+    int32_t *rg_bucket_seeds;         // [B*k]
+    int64_t *rg_bucket_gains;         // [B*k]
+    size_t rg_cap_bytes;
+    void *rg_block;
+    // scratch arena (grown on demand) and per-call results
+    void *scratch;
+    size_t scratch_bytes;
+    void *res;
+    size_t res_bytes;
+};
+
+namespace im {
+
+// error plumbing (api.cu)
+void set_error(const std::string &msg);
+im_status cuda_fail(cudaError_t e, const char *what);
+#define IM_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::im::cuda_fail(_e, #call);  \
+    } while (0)
+im_status map_dev_status(int code, const char *where);
+
+// scratch arena of a pool: returns a pointer to at least `bytes` (256-aligned)
+im_status pool_scratch(im_pool *p, size_t bytes, void **out);
+
+int num_sms();
+
+// scan.cu
+im_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t count,
+                                    const int64_t *base, void *tmp, size_t tmp_bytes,
+                                    cudaStream_t st);
+size_t scan_tmp_bytes(int64_t count);
+
+// sample.cu
+im_status sample_append(const im_graph *g, im_model model, uint64_t seed, uint64_t first,
+                        uint64_t count, im_pool *pool, cudaStream_t st);
+im_status build_lt_cdf(im_graph *g, cudaStream_t st);
+template <typename Key>
+im_status segmented_sort(Key *keys, const int64_t *seg_off, int64_t nseg, void *tmp,
+                         size_t tmp_bytes, cudaStream_t st);
+
+// index.cu
+im_status build_index(im_pool *p, cudaStream_t st);
+im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st);
+im_status launch_partition_labels(int64_t n, int32_t P, uint64_t pseed, int32_t *part,
+                                  cudaStream_t st);
+im_status max_segment_length(const int64_t *off, int64_t n, int64_t *d_out, cudaStream_t st);
+
+// cover.cu
+int32_t num_buckets(int32_t k, double delta);
+im_status greedy_plain(im_pool *p, int32_t k, int32_t *d_seeds, int64_t *d_gains,
+                       int32_t *d_nseeds, int64_t *d_cov, cudaStream_t st, int *d_status);
+im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_seeds,
+                     int64_t *d_gains, int32_t *d_nseeds, int64_t *d_cov, cudaStream_t st,
+                     int *d_status);
+
+}  // namespace im

@@ -1,0 +1,733 @@
+// sample.cu -- RRR sampling (IC reverse BFS, LT backward walk), compaction into
+// the pool's CSR, and the segmented sorts that put every set in ascending order.
+//
+// One warp owns one sample at a time and takes the next sample id from a
+// global counter (persistent kernel, dynamic balancing: set sizes are heavy
+// tailed on R-MAT graphs).  IC (Def. 3 under the IC live-edge world): the
+// warp expands up to 32 queued vertices at once; their in-edge ranges are
+// split into aligned groups of four edges, one group per lane, so each lane
+// makes one Philox call (four coins) and one 16-byte load of weights and one
+// of sources.  LT: the walk takes one step per iteration; the picked in-edge
+// (first edge whose running weight sum exceeds the draw) is found by a
+// 32-ary search over the per-vertex cumulative weights, the revisit test is a
+// warp compare against the path held in shared memory.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace im {
+
+namespace {
+
+constexpr int kSampleThreads = 256;          // 8 warps per block
+constexpr int kWarps = kSampleThreads / 32;
+constexpr int64_t kSmemVisBits = 1 << 16;    // visited bitmap in smem when n <= this
+constexpr int kPathSmem = 256;               // LT path entries mirrored in smem
+constexpr int64_t kQueueCapIC = 1 << 14;     // per-warp queue entries (first pass)
+constexpr int64_t kQueueCapLT = 1 << 12;
+constexpr int kWarpSortBytes = 4096;         // per-warp smem sort buffer
+constexpr int kBlockSortCap = 16384;         // ... by one block in shared memory (int32)
+
+struct SampleArgs {
+    uint32_t n;
+    const int64_t *in_off;
+    const int32_t *in_src;
+    const uint32_t *w;
+    const uint64_t *cdf;
+    uint64_t seed;
+    uint32_t first;
+    int64_t count;            // work items
+    const int64_t *list;      // if non-null: work item i is sample index list[i]
+    int32_t *stage;
+    int64_t stage_cap;
+    unsigned long long *stage_cursor;
+    int64_t *stage_off;       // [count of the call]
+    int32_t *sizes;           // [count of the call]; -1 marks a queue overflow
+    int32_t *queues;
+    int64_t qcap;
+    uint32_t *gvis;
+    int64_t vis_words;
+    unsigned long long *examined;
+    unsigned long long *work;
+    int64_t *ovf_list;
+    unsigned long long *ovf_count;
+    int *status;
+};
+
+__device__ __forceinline__ int64_t next_item(const SampleArgs &a, int lane) {
+    unsigned long long j = 0;
+    if (lane == 0) j = atomicAdd(a.work, 1ull);
+    j = __shfl_sync(kFull, j, 0);
+    if (j >= (unsigned long long)a.count) return -1;
+    return a.list ? a.list[j] : (int64_t)j;
+}
+
+// Move the finished set q[0..len) to the stage and record where it went.
+__device__ __forceinline__ void emit_set(const SampleArgs &a, int64_t j, const int32_t *q,
+                                         int64_t len, int lane) {
+    unsigned long long pos = 0;
+    if (lane == 0) pos = atomicAdd(a.stage_cursor, (unsigned long long)len);
+    pos = __shfl_sync(kFull, pos, 0);
+    if ((int64_t)pos + len > a.stage_cap) {
+        if (lane == 0) {
+            raise_status(a.status, kDevStageOverflow);
+            a.sizes[j] = 0;
+            a.stage_off[j] = 0;
+        }
+        return;
+    }
+    for (int64_t i = lane; i < len; i += 32) a.stage[pos + i] = q[i];
+    if (lane == 0) {
+        a.stage_off[j] = (int64_t)pos;
+        a.sizes[j] = (int32_t)len;
+    }
+}
+
+__device__ __forceinline__ void mark_overflow(const SampleArgs &a, int64_t j, int lane) {
+    if (lane == 0) {
+        a.sizes[j] = -1;
+        a.stage_off[j] = 0;
+        unsigned long long at = atomicAdd(a.ovf_count, 1ull);
+        a.ovf_list[at] = j;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// IC: stochastic reverse BFS.  Edge e of sample s is live iff lane (e & 3) of
+// Philox(s, e >> 2 (low word), e >> 34, coin tag) is below w[e].
+// ---------------------------------------------------------------------------
+template <bool kSmemVis>
+__global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
+    extern __shared__ uint32_t smem_vis[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + wib;
+    uint32_t *vis = kSmemVis ? smem_vis + (size_t)wib * a.vis_words
+                             : a.gvis + (size_t)gw * (size_t)a.vis_words;
+    int32_t *q = a.queues + (size_t)gw * (size_t)a.qcap;
+    if (kSmemVis)
+        for (int64_t i = lane; i < a.vis_words; i += 32) vis[i] = 0;
+    __syncwarp();
+    const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
+    unsigned long long exam = 0;
+    for (;;) {
+        const int64_t j = next_item(a, lane);
+        if (j < 0) break;
+        const uint32_t s = a.first + (uint32_t)j;
+        const uint32_t root = rrr_root(a.seed, s, a.n);
+        if (lane == 0) {
+            atomicOr(&vis[root >> 5], 1u << (root & 31));
+            q[0] = (int32_t)root;
+        }
+        __syncwarp();
+        int64_t head = 0, tail = 1;
+        bool overflow = false;
+        unsigned long long sexam = 0;
+        while (head < tail && !overflow) {
+            const int nb = (int)(tail - head < 32 ? tail - head : 32);
+            int64_t eb = 0, ee = 0;
+            if (lane < nb) {
+                const int32_t v = q[head + lane];
+                eb = __ldg(a.in_off + v);
+                ee = __ldg(a.in_off + v + 1);
+                sexam += (unsigned long long)(ee - eb);
+            }
+            head += nb;
+            const int64_t g0 = eb >> 2;
+            const int64_t ng = ee > eb ? ((ee - 1) >> 2) - g0 + 1 : 0;
+            const int64_t incl = warp_incl_scan<int64_t>(ng, lane);
+            const int64_t total = __shfl_sync(kFull, incl, 31);
+            for (int64_t base = 0; base < total; base += 32) {
+                const int64_t t = base + lane;
+                int owner = 0;   // first lane whose inclusive group count exceeds t
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
+                    if (c <= t) owner += step;
+                }
+                const int64_t o_incl = __shfl_sync(kFull, incl, owner);
+                const int64_t o_ng = __shfl_sync(kFull, ng, owner);
+                const int64_t o_g0 = __shfl_sync(kFull, g0, owner);
+                const int64_t o_eb = __shfl_sync(kFull, eb, owner);
+                const int64_t o_ee = __shfl_sync(kFull, ee, owner);
+                unsigned fresh = 0;
+                int32_t src[4] = {0, 0, 0, 0};
+                if (t < total) {
+                    const int64_t g = o_g0 + (t - (o_incl - o_ng));
+                    const uint4 coin = philox4x32_10(
+                        make_uint4(s, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), kStreamCoin), k0,
+                        k1);
+                    const uint4 wv = __ldg(reinterpret_cast<const uint4 *>(a.w) + g);
+                    const int4 sv = __ldg(reinterpret_cast<const int4 *>(a.in_src) + g);
+                    const uint32_t cv[4] = {coin.x, coin.y, coin.z, coin.w};
+                    const uint32_t wq[4] = {wv.x, wv.y, wv.z, wv.w};
+                    src[0] = sv.x; src[1] = sv.y; src[2] = sv.z; src[3] = sv.w;
+                    const int64_t e0 = g << 2;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int64_t e = e0 + c;
+                        if (e >= o_eb && e < o_ee && cv[c] < wq[c]) {
+                            const uint32_t u = (uint32_t)src[c];
+                            const uint32_t bit = 1u << (u & 31);
+                            if (!(atomicOr(&vis[u >> 5], bit) & bit)) fresh |= 1u << c;
+                        }
+                    }
+                }
+                const int nf = __popc(fresh);
+                const int inclf = warp_incl_scan<int>(nf, lane);
+                const int totf = __shfl_sync(kFull, inclf, 31);
+                if (totf == 0) continue;
+                if (tail + totf > a.qcap) {
+                    // drop this sample; un-mark what was just marked
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (fresh >> c & 1) {
+                            const uint32_t u = (uint32_t)src[c];
+                            atomicAnd(&vis[u >> 5], ~(1u << (u & 31)));
+                        }
+                    overflow = true;
+                    break;
+                }
+                int64_t pos = tail + inclf - nf;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (fresh >> c & 1) q[pos++] = src[c];
+                tail += totf;
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+        if (overflow) {
+            mark_overflow(a, j, lane);
+        } else {
+            emit_set(a, j, q, tail, lane);
+            exam += sexam;
+        }
+        // reset the visited bits of this sample
+        if (tail > a.vis_words) {
+            for (int64_t i = lane; i < a.vis_words; i += 32) vis[i] = 0;
+        } else {
+            for (int64_t i = lane; i < tail; i += 32) {
+                const uint32_t u = (uint32_t)q[i];
+                vis[u >> 5] = 0;
+            }
+        }
+        __syncwarp();
+    }
+    exam = warp_sum<unsigned long long>(exam);
+    if (lane == 0 && exam) atomicAdd(a.examined, exam);
+}
+
+// ---------------------------------------------------------------------------
+// LT: backward walk of the LT live-edge world.  Vertex v picks the first
+// in-edge whose running weight sum exceeds Philox(s, v, 0, pick tag).x; the
+// walk stops when nothing is picked or the picked source is already on it.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSampleThreads) k_sample_lt(SampleArgs a) {
+    __shared__ int32_t spath[kWarps][kPathSmem];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + wib;
+    int32_t *q = a.queues + (size_t)gw * (size_t)a.qcap;
+    int32_t *sp = spath[wib];
+    const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
+    unsigned long long exam = 0;
+    for (;;) {
+        const int64_t j = next_item(a, lane);
+        if (j < 0) break;
+        const uint32_t s = a.first + (uint32_t)j;
+        uint32_t cur = rrr_root(a.seed, s, a.n);
+        if (lane == 0) {
+            q[0] = (int32_t)cur;
+            sp[0] = (int32_t)cur;
+        }
+        __syncwarp();
+        int64_t len = 1;
+        bool overflow = false;
+        unsigned long long sexam = 0;
+        for (;;) {
+            const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
+            const int64_t eb = __ldg(a.in_off + cur);
+            const int64_t d = __ldg(a.in_off + cur + 1) - eb;
+            int64_t pick = -1;
+            if (d > 0) {
+                int64_t lo = 0, hi = d;
+                bool none = false;
+                while (hi - lo > 32) {
+                    const int64_t step = (hi - lo + 31) >> 5;
+                    int64_t probe = lo + (int64_t)(lane + 1) * step - 1;
+                    if (probe > hi - 1) probe = hi - 1;
+                    const bool pr = (uint64_t)x < __ldg(a.cdf + eb + probe);
+                    const unsigned bal = __ballot_sync(kFull, pr);
+                    if (!bal) {
+                        none = true;
+                        break;
+                    }
+                    const int f = __ffs(bal) - 1;
+                    const int64_t nlo = lo + (int64_t)f * step;
+                    hi = min(lo + (int64_t)(f + 1) * step, hi);
+                    lo = nlo;
+                }
+                if (!none) {
+                    const int64_t idx = lo + lane;
+                    const bool pr = idx < hi && (uint64_t)x < __ldg(a.cdf + eb + idx);
+                    const unsigned bal = __ballot_sync(kFull, pr);
+                    if (bal) pick = lo + __ffs(bal) - 1;
+                }
+            }
+            if (lane == 0) sexam += (unsigned long long)(pick >= 0 ? pick + 1 : d);
+            if (pick < 0) break;
+            const int32_t u = __ldg(a.in_src + eb + pick);
+            bool seen = false;
+            const int64_t ls = len < kPathSmem ? len : kPathSmem;
+            for (int64_t i = lane; i < ls; i += 32) seen |= sp[i] == u;
+            for (int64_t i = kPathSmem + lane; i < len; i += 32) seen |= q[i] == u;
+            if (__any_sync(kFull, seen)) break;
+            if (len >= a.qcap) {
+                overflow = true;
+                break;
+            }
+            if (lane == 0) {
+                q[len] = u;
+                if (len < kPathSmem) sp[len] = u;
+            }
+            __syncwarp();
+            ++len;
+            cur = (uint32_t)u;
+        }
+        __syncwarp();
+        if (overflow) {
+            mark_overflow(a, j, lane);
+        } else {
+            emit_set(a, j, q, len, lane);
+            exam += sexam;
+        }
+        __syncwarp();
+    }
+    exam = warp_sum<unsigned long long>(exam);
+    if (lane == 0 && exam) atomicAdd(a.examined, exam);
+}
+
+// LT cumulative weights: cdf[e] = sum of w over in-edges of dst(e) up to e.
+__global__ void k_lt_cdf(const int64_t *in_off, const uint32_t *w, uint64_t *cdf, int64_t n,
+                         int *invalid) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
+         v += nw) {
+        const int64_t b = in_off[v], e = in_off[v + 1];
+        uint64_t carry = 0;
+        for (int64_t base = b; base < e; base += 32) {
+            const int64_t i = base + lane;
+            const uint64_t x = i < e ? (uint64_t)w[i] : 0ull;
+            const uint64_t incl = warp_incl_scan<unsigned long long>(x, lane);
+            if (i < e) cdf[i] = carry + incl;
+            carry += __shfl_sync(kFull, incl, 31);
+        }
+        if (lane == 0 && carry > (1ull << 32)) atomicExch(invalid, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// segmented sort: every segment [seg_off[i], seg_off[i+1]) ascending
+// ---------------------------------------------------------------------------
+template <typename Key>
+__device__ __forceinline__ Key key_max();
+template <>
+__device__ __forceinline__ int32_t key_max<int32_t>() { return 0x7fffffff; }
+template <>
+__device__ __forceinline__ uint64_t key_max<uint64_t>() { return ~0ull; }
+
+template <typename Key>
+__device__ __forceinline__ Key warp_bitonic32(Key v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const Key o = __shfl_xor_sync(kFull, v, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+        }
+    }
+    return v;
+}
+
+// bitonic network over buf[0..P) (P a power of two) by `nthreads` threads
+template <typename Key>
+__device__ __forceinline__ void bitonic_smem(Key *buf, int P, int tid, int nthreads,
+                                             bool block_level) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += nthreads) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const Key x = buf[i], y = buf[l];
+                    const bool asc = (i & k) == 0;
+                    if ((x > y) == asc) {
+                        buf[i] = y;
+                        buf[l] = x;
+                    }
+                }
+            }
+            if (block_level) __syncthreads();
+            else __syncwarp();
+        }
+    }
+}
+
+// Copies stage segments into place (when `stage` is non-null) and sorts every
+// segment of up to 4 KB of keys with one warp; longer ones go to `big`.
+template <typename Key>
+__global__ void __launch_bounds__(256) k_sort_small(Key *dst, const int64_t *seg_off, int64_t nseg,
+                                                    const Key *stage, const int64_t *stage_off,
+                                                    int64_t *big, unsigned long long *nbig) {
+    constexpr int kCapW = kWarpSortBytes / (int)sizeof(Key);
+    __shared__ Key sbuf[8][kCapW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < nseg; i += nw) {
+        const int64_t o = seg_off[i];
+        const int64_t len = seg_off[i + 1] - o;
+        const Key *src = stage ? stage + stage_off[i] : dst + o;
+        Key *out = dst + o;
+        if (len <= 1) {
+            if (len == 1 && stage && lane == 0) out[0] = src[0];
+        } else if (len <= 32) {
+            Key v = lane < len ? src[lane] : key_max<Key>();
+            v = warp_bitonic32<Key>(v, lane);
+            if (lane < len) out[lane] = v;
+        } else if (len <= kCapW) {
+            int P = 64;
+            while (P < len) P <<= 1;
+            Key *buf = sbuf[wib];
+            for (int t = lane; t < P; t += 32) buf[t] = t < len ? src[t] : key_max<Key>();
+            __syncwarp();
+            bitonic_smem<Key>(buf, P, lane, 32, false);
+            for (int t = lane; t < len; t += 32) out[t] = buf[t];
+        } else {
+            if (stage)
+                for (int64_t t = lane; t < len; t += 32) out[t] = src[t];
+            if (lane == 0) big[atomicAdd(nbig, 1ull)] = i;
+        }
+        __syncwarp();
+    }
+}
+
+// One block per listed segment longer than a warp's buffer and at most kCap
+// keys: bitonic sort in shared memory.
+template <typename Key, int kCap>
+__global__ void __launch_bounds__(1024) k_sort_block(Key *dst, const int64_t *seg_off,
+                                                     const int64_t *big,
+                                                     const unsigned long long *nbig,
+                                                     int64_t *giant,
+                                                     unsigned long long *ngiant) {
+    extern __shared__ unsigned char sraw[];
+    Key *buf = reinterpret_cast<Key *>(sraw);
+    const int64_t nb = (int64_t)*nbig;
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t i = big[b];
+        const int64_t o = seg_off[i];
+        const int64_t len = seg_off[i + 1] - o;
+        if (len > kCap) {
+            if (threadIdx.x == 0 && giant) giant[atomicAdd(ngiant, 1ull)] = i;
+            continue;
+        }
+        int P = 64;
+        while (P < len) P <<= 1;
+        for (int t = threadIdx.x; t < P; t += blockDim.x)
+            buf[t] = t < len ? dst[o + t] : key_max<Key>();
+        __syncthreads();
+        bitonic_smem<Key>(buf, P, threadIdx.x, blockDim.x, true);
+        for (int t = threadIdx.x; t < len; t += blockDim.x) dst[o + t] = buf[t];
+        __syncthreads();
+    }
+}
+
+// Segments longer than kBlockSortCap of distinct vertex ids: mark them in an
+// n-bit bitmap (one per block) and read the bitmap back in order.
+__global__ void __launch_bounds__(1024) k_sort_giant(int32_t *dst, const int64_t *seg_off,
+                                                     const int64_t *giant,
+                                                     const unsigned long long *ngiant,
+                                                     uint32_t *bitmaps, int64_t words) {
+    __shared__ int64_t sh[33];
+    uint32_t *bm = bitmaps + (size_t)blockIdx.x * (size_t)words;
+    const int64_t ng = (int64_t)*ngiant;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t b = blockIdx.x; b < ng; b += gridDim.x) {
+        const int64_t i = giant[b];
+        const int64_t o = seg_off[i];
+        const int64_t len = seg_off[i + 1] - o;
+        for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+            const uint32_t u = (uint32_t)dst[o + t];
+            atomicOr(&bm[u >> 5], 1u << (u & 31));
+        }
+        __syncthreads();
+        const int64_t per = (words + blockDim.x - 1) / blockDim.x;
+        const int64_t w0 = (int64_t)threadIdx.x * per;
+        const int64_t w1 = min(words, w0 + per);
+        int64_t cnt = 0;
+        for (int64_t x = w0; x < w1; ++x) cnt += __popc(bm[x]);
+        // block exclusive scan of cnt
+        int64_t incl = warp_incl_scan<int64_t>(cnt, lane);
+        if (lane == 31) sh[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+            int64_t vi = warp_incl_scan<int64_t>(v, lane);
+            if (lane < (int)(blockDim.x >> 5)) sh[lane] = vi - v;
+        }
+        __syncthreads();
+        int64_t at = o + sh[warp] + incl - cnt;
+        __syncthreads();
+        for (int64_t x = w0; x < w1; ++x) {
+            uint32_t bits = bm[x];
+            while (bits) {
+                const int bpos = __ffs(bits) - 1;
+                bits &= bits - 1;
+                dst[at++] = (int32_t)(x * 32 + bpos);
+            }
+        }
+        __syncthreads();
+        for (int64_t x = w0; x < w1; ++x) bm[x] = 0;
+        __syncthreads();
+    }
+}
+
+int blocks_for(const void *kernel, int threads, size_t smem) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * num_sms();
+}
+
+}  // namespace
+
+template <typename Key>
+im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, const Key *stage,
+                              const int64_t *stage_off, void *tmp, size_t tmp_bytes,
+                              int64_t *ngiant_host, cudaStream_t st) {
+    // tmp layout: [2 counters][big list nseg][giant list nseg]
+    if (tmp_bytes < (size_t)(2 + 2 * nseg) * 8) return IM_ERR_INVALID_ARG;
+    unsigned long long *ctr = (unsigned long long *)tmp;
+    int64_t *big = (int64_t *)tmp + 2;
+    int64_t *giant = big + nseg;
+    IM_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), st));
+    if (nseg == 0) return IM_OK;
+    const int gs = blocks_for((const void *)k_sort_small<Key>, 256, 0);
+    k_sort_small<Key><<<gs, 256, 0, st>>>(keys, seg_off, nseg, stage, stage_off, big, ctr);
+    constexpr int kCap = sizeof(Key) == 4 ? kBlockSortCap : kSortedKeyCap64;
+    static_assert(kBlockSortCap * 4 == kSortedKeyCap64 * 8, "smem sized for both key widths");
+    const size_t smem = (size_t)kCap * sizeof(Key);
+    IM_CUDA(cudaFuncSetAttribute(k_sort_block<Key, kCap>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sort_block<Key, kCap><<<num_sms(), 1024, smem, st>>>(keys, seg_off, big, ctr,
+                                                          giant, ctr + 1);
+    IM_CUDA(cudaGetLastError());
+    if (ngiant_host) {
+        unsigned long long ng = 0;
+        IM_CUDA(cudaMemcpyAsync(&ng, ctr + 1, sizeof(ng), cudaMemcpyDeviceToHost, st));
+        IM_CUDA(cudaStreamSynchronize(st));
+        *ngiant_host = (int64_t)ng;
+    }
+    return IM_OK;
+}
+
+template <typename Key>
+im_status segmented_sort(Key *keys, const int64_t *seg_off, int64_t nseg, void *tmp,
+                         size_t tmp_bytes, cudaStream_t st) {
+    // segments longer than the block cap stay as they are (callers treat them
+    // as unsorted)
+    return segmented_sort_impl<Key>(keys, seg_off, nseg, nullptr, nullptr, tmp, tmp_bytes,
+                                    nullptr, st);
+}
+template im_status segmented_sort<uint64_t>(uint64_t *, const int64_t *, int64_t, void *, size_t,
+                                            cudaStream_t);
+
+im_status build_lt_cdf(im_graph *g, cudaStream_t st) {
+    if (g->lt_cdf) return IM_OK;
+    IM_CUDA(cudaMalloc(&g->lt_cdf, (size_t)std::max<int64_t>(g->m, 1) * sizeof(uint64_t)));
+    int *d_invalid = nullptr;
+    IM_CUDA(cudaMalloc(&d_invalid, sizeof(int)));
+    IM_CUDA(cudaMemsetAsync(d_invalid, 0, sizeof(int), st));
+    k_lt_cdf<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->w, g->lt_cdf, g->n, d_invalid);
+    int invalid = 0;
+    IM_CUDA(cudaMemcpyAsync(&invalid, d_invalid, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IM_CUDA(cudaStreamSynchronize(st));
+    cudaFree(d_invalid);
+    g->lt_valid = invalid ? 0 : 1;
+    return IM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sample(G, count): append sample ids first .. first+count-1 to the pool.
+// ---------------------------------------------------------------------------
+im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint64_t first,
+                        uint64_t count, im_pool *pool, cudaStream_t st) {
+    im_graph *g = const_cast<im_graph *>(gc);
+    if (model == IM_LT) {
+        im_status s = build_lt_cdf(g, st);
+        if (s != IM_OK) return s;
+        if (!g->lt_valid) {
+            set_error("LT sampling needs every vertex's in-weights to sum to at most 2^32");
+            return IM_ERR_INVALID_ARG;
+        }
+    }
+    if (count == 0) return IM_OK;
+    if (pool->theta + (int64_t)count > pool->max_sets) {
+        set_error("pool max_sets exceeded");
+        return IM_ERR_CAPACITY;
+    }
+    const int64_t cnt = (int64_t)count;
+    const int64_t n = g->n;
+    const bool smem_vis = model == IM_IC && n <= kSmemVisBits;
+    const int64_t vis_words = (n + 31) / 32;
+
+    // launch shape: persistent, occupancy-sized
+    const void *kern = model == IM_LT ? (const void *)k_sample_lt
+                       : smem_vis   ? (const void *)k_sample_ic<true>
+                                    : (const void *)k_sample_ic<false>;
+    const size_t dyn_smem = smem_vis ? (size_t)kWarps * vis_words * 4 : 0;
+    if (smem_vis && dyn_smem > 48 * 1024)
+        IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dyn_smem));
+    int blocks = blocks_for(kern, kSampleThreads, dyn_smem);
+    // global visited bitmaps are n bits per warp: keep them within ~4 GB
+    if (model == IM_IC && !smem_vis) {
+        int64_t cap_blocks = std::max<int64_t>(
+            num_sms(), (int64_t)(4ll << 30) / ((int64_t)kWarps * vis_words * 4));
+        blocks = (int)std::min<int64_t>(blocks, cap_blocks);
+    }
+    const int64_t warps = (int64_t)blocks * kWarps;
+    const int64_t qcap = std::min<int64_t>(n, model == IM_LT ? kQueueCapLT : kQueueCapIC);
+
+    // scratch layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    const size_t o_ctr = take(8 * sizeof(unsigned long long));
+    const size_t o_soff = take((size_t)cnt * 8);
+    const size_t o_sizes = take((size_t)cnt * 4);
+    const size_t o_ovf = take((size_t)cnt * 8);
+    const size_t o_scan = take(scan_tmp_bytes(cnt));
+    const size_t o_sort = take((size_t)(2 + 2 * cnt) * 8);
+    const size_t o_q = take((size_t)warps * qcap * 4);
+    const size_t o_vis = take(model == IM_IC && !smem_vis ? (size_t)warps * vis_words * 4 : 0);
+    void *base = nullptr;
+    im_status rs = pool_scratch(pool, off, &base);
+    if (rs != IM_OK) return rs;
+    char *B = (char *)base;
+    unsigned long long *ctr = (unsigned long long *)(B + o_ctr);
+    // ctr: 0 work, 1 stage cursor, 2 examined, 3 overflow count, 4 status (int)
+    IM_CUDA(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), st));
+    if (o_vis && model == IM_IC && !smem_vis)
+        IM_CUDA(cudaMemsetAsync(B + o_vis, 0, (size_t)warps * vis_words * 4, st));
+
+    SampleArgs a;
+    a.n = (uint32_t)n;
+    a.in_off = g->in_off;
+    a.in_src = g->in_src;
+    a.w = g->w;
+    a.cdf = g->lt_cdf;
+    a.seed = seed;
+    a.first = (uint32_t)first;
+    a.count = cnt;
+    a.list = nullptr;
+    a.stage = pool->set_ids;                      // the index buffer doubles as the stage
+    a.stage_cap = pool->max_entries - pool->total;
+    a.stage_cursor = ctr + 1;
+    a.stage_off = (int64_t *)(B + o_soff);
+    a.sizes = (int32_t *)(B + o_sizes);
+    a.queues = (int32_t *)(B + o_q);
+    a.qcap = qcap;
+    a.gvis = (uint32_t *)(B + o_vis);
+    a.vis_words = vis_words;
+    a.examined = ctr + 2;
+    a.work = ctr;
+    a.ovf_list = (int64_t *)(B + o_ovf);
+    a.ovf_count = ctr + 3;
+    a.status = (int *)(ctr + 4);
+    pool->index_valid = false;
+    pool->pkeys_valid = false;
+
+    auto launch = [&](int nblocks) {
+        if (model == IM_LT) k_sample_lt<<<nblocks, kSampleThreads, 0, st>>>(a);
+        else if (smem_vis) k_sample_ic<true><<<nblocks, kSampleThreads, dyn_smem, st>>>(a);
+        else k_sample_ic<false><<<nblocks, kSampleThreads, 0, st>>>(a);
+    };
+    launch(blocks);
+    IM_CUDA(cudaGetLastError());
+
+    unsigned long long hc[5];
+    IM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    IM_CUDA(cudaStreamSynchronize(st));
+    int dev_status = (int)(hc[4] & 0xffffffffu);
+    if (dev_status == kDevOk && hc[3] > 0 && qcap < n) {
+        // second pass for sets longer than the per-warp queue: a few warps
+        // with queues of n entries re-run exactly those samples
+        const int64_t novf = (int64_t)hc[3];
+        int nb2 = (int)std::max<int64_t>(1, std::min<int64_t>((novf + kWarps - 1) / kWarps,
+                                                              num_sms()));
+        const int64_t warps2 = (int64_t)nb2 * kWarps;
+        const size_t need2 = (size_t)warps2 * (size_t)n * 4 +
+                             (model == IM_IC && !smem_vis ? (size_t)warps2 * vis_words * 4 : 0);
+        int32_t *q2 = nullptr;
+        IM_CUDA(cudaMallocAsync((void **)&q2, need2, st));
+        uint32_t *vis2 = (uint32_t *)((char *)q2 + (size_t)warps2 * (size_t)n * 4);
+        if (model == IM_IC && !smem_vis)
+            IM_CUDA(cudaMemsetAsync(vis2, 0, (size_t)warps2 * vis_words * 4, st));
+        IM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st));
+        SampleArgs a2 = a;
+        a2.list = a.ovf_list;
+        a2.count = novf;
+        a2.queues = q2;
+        a2.qcap = n;
+        a2.gvis = vis2;
+        a2.ovf_list = a.ovf_list + cnt;   // never written: qcap = n cannot overflow
+        a = a2;
+        launch(nb2);
+        IM_CUDA(cudaGetLastError());
+        IM_CUDA(cudaFreeAsync(q2, st));
+        IM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        IM_CUDA(cudaStreamSynchronize(st));
+        dev_status = (int)(hc[4] & 0xffffffffu);
+    }
+    if (dev_status != kDevOk) {
+        if (dev_status == kDevStageOverflow) {
+            set_error("pool max_entries exceeded while sampling");
+            return IM_ERR_CAPACITY;
+        }
+        return map_dev_status(dev_status, "sampling");
+    }
+    const int64_t added = (int64_t)hc[1];
+
+    // set_off[theta .. theta+cnt] = set_off[theta] + exclusive scan of sizes
+    int64_t *so = pool->set_off + pool->theta;
+    rs = exclusive_scan_i32_to_i64(a.sizes, so, cnt, so, B + o_scan, scan_tmp_bytes(cnt), st);
+    if (rs != IM_OK) return rs;
+    // copy stage -> members and sort each set ascending
+    int64_t ngiant = 0;
+    uint32_t *gbm = nullptr;
+    const int64_t gwords = vis_words;
+    // giant sets (> block sort cap) need an n-bit bitmap per block
+    rs = segmented_sort_impl<int32_t>(pool->members, so, cnt, a.stage, a.stage_off, B + o_sort,
+                                      (size_t)(2 + 2 * cnt) * 8, &ngiant, st);
+    if (rs != IM_OK) return rs;
+    if (ngiant > 0) {
+        const int blocks3 = (int)std::min<int64_t>(ngiant, num_sms());
+        IM_CUDA(cudaMallocAsync((void **)&gbm, (size_t)blocks3 * gwords * 4, st));
+        IM_CUDA(cudaMemsetAsync(gbm, 0, (size_t)blocks3 * gwords * 4, st));
+        unsigned long long *sctr = (unsigned long long *)(B + o_sort);
+        int64_t *giant = (int64_t *)(B + o_sort) + 2 + cnt;
+        k_sort_giant<<<blocks3, 1024, 0, st>>>(pool->members, so, giant, sctr + 1, gbm, gwords);
+        IM_CUDA(cudaGetLastError());
+        IM_CUDA(cudaFreeAsync(gbm, st));
+    }
+    pool->theta += cnt;
+    pool->total += added;
+    pool->examined += (int64_t)hc[2];
+    IM_CUDA(cudaStreamSynchronize(st));
+    return IM_OK;
+}
+
+}  // namespace im

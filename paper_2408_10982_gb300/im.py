@@ -1,0 +1,314 @@
+"""Thin ctypes binding over libim.so (C ABI in include/im.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Arrays may be numpy arrays (host), torch tensors (host or CUDA) or
+raw integer addresses; streams may be None (torch's current stream when
+torch has CUDA, else the legacy default stream), a torch.cuda.Stream or a raw
+cudaStream_t address.  The library must be built (build.build_library());
+loading fails loudly otherwise -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+IM_OK = 0
+IM_ERR_INVALID_ARG = -1
+IM_ERR_OOM = -2
+IM_ERR_CUDA = -3
+IM_ERR_TIMEOUT = -4
+IM_ERR_CAPACITY = -5
+IM_ERR_BUSY = -6
+IM_ERR_UNSUPPORTED = -7
+
+IM_IC, IM_LT = 0, 1
+IM_GREEDY_PLAIN, IM_RANDGREEDI = 0, 1
+
+
+class ImError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class CoverOpts(ctypes.Structure):
+    """im_cover_opts (see include/im.h)."""
+    _fields_ = [("algo", ctypes.c_int32), ("partitions", ctypes.c_int32),
+                ("alpha_num", ctypes.c_int32), ("alpha_den", ctypes.c_int32),
+                ("delta", ctypes.c_double), ("partition_seed", ctypes.c_uint64),
+                ("fused", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def cover_opts(algo: int = IM_GREEDY_PLAIN, partitions: int = 148, alpha: tuple = (1, 1),
+               delta: float = 0.077, partition_seed: int = 42, fused: bool = True) -> CoverOpts:
+    return CoverOpts(algo, partitions, alpha[0], alpha[1], delta, partition_seed, int(fused), 0)
+
+
+_LIB = None
+
+
+def lib():
+    """Load libim.so (must already be built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libim.so is not built ({path}); run "
+                               "paper_2408_10982_gb300.build.build_library()")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sigs = {
+            "im_status_str": ([ctypes.c_int], ctypes.c_char_p),
+            "im_last_error": ([], ctypes.c_char_p),
+            "im_device_info": ([vp, vp], ctypes.c_int),
+            "im_graph_create": ([vp, vp, vp, i64, i64, vp, pp], ctypes.c_int),
+            "im_graph_destroy": ([vp], ctypes.c_int),
+            "im_graph_info": ([vp, vp, vp, vp], ctypes.c_int),
+            "im_pool_create": ([vp, i64, i64, pp], ctypes.c_int),
+            "im_pool_destroy": ([vp], ctypes.c_int),
+            "im_pool_reset": ([vp], ctypes.c_int),
+            "im_pool_info": ([vp, vp, vp, vp], ctypes.c_int),
+            "im_sample_rrr": ([vp, ctypes.c_int, u64, u64, u64, vp, vp], ctypes.c_int),
+            "im_pool_export": ([vp, vp, vp, vp], ctypes.c_int),
+            "im_pool_index": ([vp, vp], ctypes.c_int),
+            "im_index_export": ([vp, vp, vp, vp], ctypes.c_int),
+            "im_max_k_cover": ([vp, i32, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+            "im_randgreedi_details": ([vp] + [vp] * 12 + [vp], ctypes.c_int),
+            "im_partition": ([i64, i32, u64, vp, vp], ctypes.c_int),
+        }
+        for name, (args, res) in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = L
+    return _LIB
+
+
+def status_str(s: int) -> str:
+    return lib().im_status_str(s).decode()
+
+
+def last_error() -> str:
+    return lib().im_last_error().decode()
+
+
+def _check(st: int, what: str):
+    if st != IM_OK:
+        raise ImError(st, f"{what}: {status_str(st)} ({last_error()})")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as an array")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# --- one function per C entry point (same names, same argument order) -------
+
+def im_device_info():
+    sms, dev = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().im_device_info(ctypes.byref(sms), ctypes.byref(dev)), "im_device_info")
+    return sms.value, dev.value
+
+
+def im_graph_create(in_off, in_src, w, n: int, m: int, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().im_graph_create(_ptr(in_off), _ptr(in_src), _ptr(w), n, m, _stream(stream),
+                                 ctypes.byref(h)), "im_graph_create")
+    return h
+
+
+def im_graph_destroy(g):
+    _check(lib().im_graph_destroy(g), "im_graph_destroy")
+
+
+def im_graph_info(g):
+    n, m, lt = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().im_graph_info(g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(lt)),
+           "im_graph_info")
+    return n.value, m.value, lt.value
+
+
+def im_pool_create(g, max_sets: int, max_entries: int):
+    h = ctypes.c_void_p()
+    _check(lib().im_pool_create(g, max_sets, max_entries, ctypes.byref(h)), "im_pool_create")
+    return h
+
+
+def im_pool_destroy(p):
+    _check(lib().im_pool_destroy(p), "im_pool_destroy")
+
+
+def im_pool_reset(p):
+    _check(lib().im_pool_reset(p), "im_pool_reset")
+
+
+def im_pool_info(p):
+    t, T, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().im_pool_info(p, ctypes.byref(t), ctypes.byref(T), ctypes.byref(e)),
+           "im_pool_info")
+    return t.value, T.value, e.value
+
+
+def im_sample_rrr(g, model: int, seed: int, first_sample_id: int, num_samples: int, pool,
+                  stream=None):
+    _check(lib().im_sample_rrr(g, model, seed, first_sample_id, num_samples, pool,
+                               _stream(stream)), "im_sample_rrr")
+
+
+def im_pool_export(p, set_off, members, stream=None):
+    _check(lib().im_pool_export(p, _ptr(set_off), _ptr(members), _stream(stream)),
+           "im_pool_export")
+
+
+def im_pool_index(p, stream=None):
+    _check(lib().im_pool_index(p, _stream(stream)), "im_pool_index")
+
+
+def im_index_export(p, vtx_off, set_ids, stream=None):
+    _check(lib().im_index_export(p, _ptr(vtx_off), _ptr(set_ids), _stream(stream)),
+           "im_index_export")
+
+
+def im_max_k_cover(p, k: int, opts: CoverOpts | None, seeds, gains, num_seeds, coverage,
+                   stream=None):
+    _check(lib().im_max_k_cover(p, k, None if opts is None else ctypes.byref(opts), _ptr(seeds),
+                                _ptr(gains), _ptr(num_seeds), _ptr(coverage), _stream(stream)),
+           "im_max_k_cover")
+
+
+def im_randgreedi_details(p, local_seeds=None, local_gains=None, local_n=None, local_cov=None,
+                          thr=None, bucket_cov=None, bucket_n=None, bucket_seeds=None,
+                          bucket_gains=None, stream=None):
+    P, B, ch = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().im_randgreedi_details(
+        p, ctypes.byref(P), ctypes.byref(B), _ptr(local_seeds), _ptr(local_gains), _ptr(local_n),
+        _ptr(local_cov), _ptr(thr), _ptr(bucket_cov), _ptr(bucket_n), _ptr(bucket_seeds),
+        _ptr(bucket_gains), ctypes.byref(ch), _stream(stream)), "im_randgreedi_details")
+    return P.value, B.value, ch.value
+
+
+def im_partition(n: int, P: int, partition_seed: int, part, stream=None):
+    _check(lib().im_partition(n, P, partition_seed, _ptr(part), _stream(stream)), "im_partition")
+
+
+# --- convenience wrappers (still only marshalling) ---------------------------
+
+class Graph:
+    """Owns an im_graph built from an inputs.Graph (host arrays)."""
+
+    def __init__(self, g, stream=None):
+        self.n, self.m = int(g.n), int(g.m)
+        self.handle = im_graph_create(np.ascontiguousarray(g.in_off, np.int64),
+                                      np.ascontiguousarray(g.in_src, np.int32),
+                                      np.ascontiguousarray(g.w, np.uint32), self.n, self.m, stream)
+
+    def close(self):
+        if self.handle is not None:
+            im_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class CoverResult:
+    seeds: np.ndarray
+    gains: np.ndarray
+    coverage: int
+
+
+class Pool:
+    """Owns an im_pool; numpy in, numpy out."""
+
+    def __init__(self, graph: Graph, max_sets: int, max_entries: int):
+        self.graph = graph
+        self.handle = im_pool_create(graph.handle, max_sets, max_entries)
+
+    def sample(self, model: int, seed: int, first: int, count: int, stream=None):
+        im_sample_rrr(self.graph.handle, model, seed, first, count, self.handle, stream)
+
+    def info(self):
+        return im_pool_info(self.handle)
+
+    def export(self, stream=None):
+        theta, total, _ = self.info()
+        set_off = np.zeros(theta + 1, np.int64)
+        members = np.zeros(max(total, 1), np.int32)
+        im_pool_export(self.handle, set_off, members, stream)
+        return set_off, members[:total]
+
+    def index(self, stream=None):
+        theta, total, _ = self.info()
+        vtx_off = np.zeros(self.graph.n + 1, np.int64)
+        set_ids = np.zeros(max(total, 1), np.int32)
+        im_index_export(self.handle, vtx_off, set_ids, stream)
+        return vtx_off, set_ids[:total]
+
+    def cover(self, k: int, opts: CoverOpts | None = None, stream=None) -> CoverResult:
+        seeds = np.zeros(k, np.int32)
+        gains = np.zeros(k, np.int64)
+        ns = np.zeros(1, np.int32)
+        cov = np.zeros(1, np.int64)
+        im_max_k_cover(self.handle, k, opts, seeds, gains, ns, cov, stream)
+        return CoverResult(seeds[: ns[0]].copy(), gains[: ns[0]].copy(), int(cov[0]))
+
+    def randgreedi_details(self, k: int, P: int, B: int, stream=None) -> dict:
+        d = dict(local_seeds=np.zeros(P * k, np.int32), local_gains=np.zeros(P * k, np.int64),
+                 local_n=np.zeros(P, np.int32), local_cov=np.zeros(P, np.int64),
+                 thr=np.zeros(B, np.int64), bucket_cov=np.zeros(B, np.int64),
+                 bucket_n=np.zeros(B, np.int32), bucket_seeds=np.zeros(B * k, np.int32),
+                 bucket_gains=np.zeros(B * k, np.int64))
+        P2, B2, chosen = im_randgreedi_details(self.handle, stream=stream, **d)
+        assert (P2, B2) == (P, B)
+        d["local_seeds"] = d["local_seeds"].reshape(P, k)
+        d["local_gains"] = d["local_gains"].reshape(P, k)
+        d["bucket_seeds"] = d["bucket_seeds"].reshape(B, k)
+        d["bucket_gains"] = d["bucket_gains"].reshape(B, k)
+        d["chosen"] = chosen
+        return d
+
+    def close(self):
+        if self.handle is not None:
+            im_pool_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,237 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+RRR sets, covering subsets, partitions, seeds, gains and coverage are integer
+results: the bar is bit-exact equality.  Set ids inside one S(v) are compared
+as sorted lists (their order is unspecified).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_10982_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def im():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_10982_gb300 import build, im as imm
+    build.build_library()
+    O.build()
+    return imm
+
+
+def gpu_pool(im, g, model, seed, ids, cap_entries=None):
+    G = im.Graph(g)
+    theta = sum(c for _, c in ids)
+    cap = cap_entries if cap_entries is not None else max(1, theta) * g.n
+    P = im.Pool(G, max(theta, 1), min(cap, 1 << 31))
+    for first, count in ids:
+        P.sample(model, seed, first, count)
+    return G, P
+
+
+def oracle_pool(g, model, seed, ids):
+    parts = [O.sample(model, g, seed, f, c) for f, c in ids]
+    set_off = [np.zeros(1, np.int64)]
+    members = []
+    base = 0
+    ex = 0
+    for p in parts:
+        set_off.append(p.set_off[1:] + base)
+        members.append(p.members)
+        base += int(p.set_off[-1])
+        ex += p.examined
+    return O.Pool(np.concatenate(set_off), np.concatenate(members) if members else
+                  np.zeros(0, np.int32), ex)
+
+
+def assert_pool_equal(im, P, ref):
+    set_off, members = P.export()
+    assert set_off.shape == ref.set_off.shape
+    assert np.array_equal(set_off, ref.set_off)
+    assert np.array_equal(members, ref.members)
+    theta, total, examined = P.info()
+    assert examined == ref.examined
+
+
+def assert_index_equal(P, g, ref):
+    vtx_off, set_ids = P.index()
+    rv, rs = O.invert(g.n, ref)
+    assert np.array_equal(vtx_off, rv)
+    for v in range(g.n):
+        a, b = vtx_off[v], vtx_off[v + 1]
+        if b - a > 1:
+            assert np.array_equal(np.sort(set_ids[a:b]), rs[a:b]), v
+        elif b - a == 1:
+            assert set_ids[a] == rs[a]
+
+
+# --- sampling ---------------------------------------------------------------
+
+def test_ic_small_rmat_full(im):
+    """R-MAT scale 10, IC p = 0.1, 16,384 sets: the whole pool bit-exact."""
+    g = inputs.graph_small_ic()
+    G, P = gpu_pool(im, g, im.IM_IC, 42, [(0, 16384)])
+    ref = O.sample(O.IC, g, 42, 0, 16384)
+    assert_pool_equal(im, P, ref)
+    assert_index_equal(P, g, ref)
+    c = P.cover(16)
+    rc = O.greedy(g.n, ref, O.invert(g.n, ref), 16)
+    assert c.seeds.tolist() == rc.seeds.tolist()
+    assert c.gains.tolist() == rc.gains.tolist()
+    assert c.coverage == rc.coverage
+
+
+@pytest.mark.parametrize("wmode", ["random", "0.3", "0.05", "zero", "one", "lt"])
+@pytest.mark.parametrize("theta", [1, 31, 33, 1000])
+def test_ic_random_graphs(im, wmode, theta):
+    g = inputs.random_graph(60, 400, 7, wmode)
+    G, P = gpu_pool(im, g, im.IM_IC, 1234, [(0, theta)])
+    assert_pool_equal(im, P, O.sample(O.IC, g, 1234, 0, theta))
+
+
+@pytest.mark.parametrize("wmode", ["lt", "lt_random", "zero"])
+@pytest.mark.parametrize("theta", [1, 33, 2000])
+def test_lt_random_graphs(im, wmode, theta):
+    g = inputs.random_graph(60, 500, 9, wmode)
+    G, P = gpu_pool(im, g, im.IM_LT, 99, [(0, theta)])
+    assert_pool_equal(im, P, O.sample(O.LT, g, 99, 0, theta))
+
+
+def test_lt_rmat_scale14(im):
+    g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+    G, P = gpu_pool(im, g, im.IM_LT, 42, [(0, 50000)])
+    ref = O.sample(O.LT, g, 42, 0, 50000)
+    assert_pool_equal(im, P, ref)
+    assert_index_equal(P, g, ref)
+
+
+def test_ic_rmat_global_visited(im):
+    """n > 65,536 puts the visited bitmaps in global memory."""
+    g = inputs.rmat_graph(1 << 17, 1 << 21, 42, "trivalency")
+    G, P = gpu_pool(im, g, im.IM_IC, 5, [(0, 20000)])
+    assert_pool_equal(im, P, O.sample(O.IC, g, 5, 0, 20000))
+
+
+def test_ic_giant_sets_overflow_path(im):
+    """Sets larger than a warp's queue (16,384) and than a block sort (16,384)."""
+    g = inputs.rmat_graph(1 << 15, 1 << 19, 3, "ic0.9")
+    G, P = gpu_pool(im, g, im.IM_IC, 8, [(0, 300)], cap_entries=300 * (1 << 15))
+    ref = O.sample(O.IC, g, 8, 0, 300)
+    assert np.diff(ref.set_off).max() > 16384
+    assert_pool_equal(im, P, ref)
+
+
+def test_append_matches_one_call(im):
+    g = inputs.random_graph(50, 300, 4, "0.25")
+    G, P = gpu_pool(im, g, im.IM_IC, 77, [(0, 100), (100, 37), (137, 500)])
+    assert_pool_equal(im, P, O.sample(O.IC, g, 77, 0, 637))
+    G2, P2 = gpu_pool(im, g, im.IM_IC, 77, [(1000, 200), (5, 10)])
+    assert_pool_equal(im, P2, oracle_pool(g, O.IC, 77, [(1000, 200), (5, 10)]))
+
+
+def test_capacity_error_leaves_pool_unchanged(im):
+    g = inputs.random_graph(50, 300, 4, "one")
+    G = im.Graph(g)
+    P = im.Pool(G, 100, 120)
+    with pytest.raises(im.ImError) as e:
+        P.sample(im.IM_IC, 1, 0, 100)
+    assert e.value.status == im.IM_ERR_CAPACITY
+    assert P.info()[:2] == (0, 0)
+    P2 = im.Pool(G, 10, 10 * 50)
+    with pytest.raises(im.ImError):
+        P2.sample(im.IM_IC, 1, 0, 11)
+
+
+def test_invalid_graph_rejected(im):
+    g = inputs.random_graph(20, 50, 4, "0.5")
+    bad = g.in_src.copy()
+    bad[3] = 99
+    with pytest.raises(im.ImError) as e:
+        im.im_graph_create(g.in_off, bad, g.w, g.n, g.m)
+    assert e.value.status == im.IM_ERR_INVALID_ARG
+
+
+# --- partition and covers ---------------------------------------------------
+
+def test_partition_labels(im):
+    part = np.zeros(100000, np.int32)
+    im.im_partition(100000, 148, 42, part)
+    assert np.array_equal(part, O.partition(100000, 148, 42))
+
+
+@pytest.mark.parametrize("k", [1, 3, 16, 64])
+def test_greedy_plain(im, k):
+    g = inputs.rmat_graph(4096, 65536, 11, "ic0.05")
+    G, P = gpu_pool(im, g, im.IM_IC, 3, [(0, 20000)])
+    ref = O.sample(O.IC, g, 3, 0, 20000)
+    c = P.cover(k)
+    rc = O.greedy(g.n, ref, O.invert(g.n, ref), k)
+    assert c.seeds.tolist() == rc.seeds.tolist()
+    assert c.gains.tolist() == rc.gains.tolist()
+    assert c.coverage == rc.coverage
+
+
+def test_greedy_stops_at_zero_gain(im):
+    g = inputs.random_graph(30, 60, 2, "zero")      # every set is a singleton
+    G, P = gpu_pool(im, g, im.IM_IC, 3, [(0, 10)])
+    ref = O.sample(O.IC, g, 3, 0, 10)
+    c = P.cover(25)
+    rc = O.greedy(g.n, ref, O.invert(g.n, ref), 25)
+    assert len(c.seeds) == len(rc.seeds) < 25
+    assert c.seeds.tolist() == rc.seeds.tolist()
+    assert c.coverage == rc.coverage == 10
+
+
+def test_empty_pool_cover(im):
+    g = inputs.random_graph(30, 60, 2, "0.5")
+    G = im.Graph(g)
+    P = im.Pool(G, 10, 100)
+    c = P.cover(5)
+    assert len(c.seeds) == 0 and c.coverage == 0
+
+
+def _rg_compare(im, g, model, theta, k, Pn, alpha, delta, fused, seed=42, pseed=42):
+    G, P = gpu_pool(im, g, model, seed, [(0, theta)])
+    ref = O.sample(model, g, seed, 0, theta)
+    inv = O.invert(g.n, ref)
+    trunc = O.trunc_count(k, *alpha)
+    r = O.randgreedi(g.n, ref, inv, k, Pn, pseed, trunc, delta)
+    opts = im.cover_opts(im.IM_RANDGREEDI, Pn, alpha, delta, pseed, fused)
+    c = P.cover(k, opts)
+    B = O.num_buckets(k, delta)
+    d = P.randgreedi_details(k, Pn, B)
+    assert np.array_equal(d["local_n"], r.local_n)
+    for p in range(Pn):
+        n_p = r.local_n[p]
+        assert d["local_seeds"][p, :n_p].tolist() == r.local_seeds[p, :n_p].tolist(), p
+        assert d["local_gains"][p, :n_p].tolist() == r.local_gains[p, :n_p].tolist(), p
+    assert np.array_equal(d["local_cov"], r.local_cov)
+    assert np.array_equal(d["thr"], r.thr)
+    assert np.array_equal(d["bucket_n"], r.buckets.n)
+    assert np.array_equal(d["bucket_cov"], r.buckets.cov)
+    for b in range(B):
+        nb = r.buckets.n[b]
+        assert d["bucket_seeds"][b, :nb].tolist() == r.buckets.seeds[b, :nb].tolist(), b
+        assert d["bucket_gains"][b, :nb].tolist() == r.buckets.gains[b, :nb].tolist(), b
+    assert d["chosen"] == r.chosen
+    assert c.seeds.tolist() == r.seeds.tolist()
+    assert c.gains.tolist() == r.gains.tolist()
+    assert c.coverage == r.coverage
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("Pn,alpha", [(148, (1, 4)), (7, (1, 1)), (1, (1, 2))])
+def test_randgreedi_lt(im, fused, Pn, alpha):
+    g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+    _rg_compare(im, g, im.IM_LT, 30000, 100 if Pn == 148 else 20, Pn, alpha, 0.077, fused)
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_randgreedi_ic_small(im, fused):
+    g = inputs.graph_small_ic()
+    _rg_compare(im, g, im.IM_IC, 16384, 16, 148, (1, 4), 0.077, fused)
