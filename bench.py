@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the RIS hot path (GreediRIS, arXiv 2408.10982) on GB300.
+
+One step = the whole hot path over one batch of synthetic input:
+  RRR sampling of theta sets (im_sample_rrr: walk kernel, scan, per-set sort)
+  -> covering-subset index (histogram, scan, scatter)
+  -> plain greedy max-k-cover                        (im_max_k_cover, greedy)
+  -> RandGreedi: 148 vertex parts, local greedy + streaming threshold buckets,
+     truncated to the first ceil(k/4) local seeds    (im_max_k_cover, RandGreedi)
+Workload: R-MAT scale 20 (1,048,576 vertices, 16,777,216 edges, a/b/c/d =
+0.57/0.19/0.19/0.05, seed 42), LT weights 1/in-degree quantised to uint32,
+theta = 4,194,304, k = 100, delta = 0.077.
+
+`value` is RRR edges examined per second over whole steps (the edges the
+LT cumulative-weight search decides over, identical to the oracle's count),
+with the graph resident in HBM.  `e2e` is the same metric through the C ABI
+from pinned host arrays: graph upload, LT index build, sampling, both covers
+and the read-back of seeds every step.
+
+--impl reference runs the CPU oracle (oracle/, the plain definition) on a
+bounded sample of the same workload on rank 0.
+
+Multi-GPU: one process per GPU; every rank runs its own replica with its own
+disjoint sample ids (weak scaling, no data-path collective; the path's only
+exchange step is not needed when ranks solve independent problems).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2408_10982_gb300 import inputs  # noqa: E402
+
+THETA = 4_194_304
+K = 100
+PARTS = 148
+ALPHA = (1, 4)
+DELTA = 0.077
+SEED = 42
+METRIC = "RRR edges/s + max-k-cover ms (HBM %); served q/s, p50/p99 vs plain; bit-exact"
+WORKLOAD = ("rmat20-lt: R-MAT scale 20 (1,048,576 vertices, 16,777,216 edges, a/b/c=0.57/0.19/0.19, "
+            "seed 42), LT 1/in-degree as uint32, theta=4,194,304 RRR sets, k=100; plain greedy "
+            "+ RandGreedi (148 partitions, streamed top ceil(k/4), delta=0.077)")
+# DRAM bytes per launch from an ncu capture, valid while the kernel source is
+# unchanged (sha256 of the file that holds it).
+TRAFFIC: dict = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--theta", type=int, default=THETA, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def src_sha(name: str) -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2408_10982_gb300", "csrc", name)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm, and the cpu_baseline of our arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step(g, first: int, count: int):
+    """Oracle over a bounded sample: sample, covering subsets, both covers."""
+    import oracle as O
+    t0 = time.perf_counter()
+    pool = O.sample(O.LT, g, SEED, first, count)
+    inv = O.invert(g.n, pool)
+    O.greedy(g.n, pool, inv, K)
+    O.randgreedi(g.n, pool, inv, K, PARTS, SEED, O.trunc_count(K, *ALPHA), DELTA)
+    return time.perf_counter() - t0, pool
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    g = inputs.graph_lt_scale20(SEED)
+    count = 65536
+    for w in range(args.warmup):
+        oracle_step(g, w * count, count)
+    total_t, total_e = 0.0, 0
+    for s in range(args.steps):
+        dt, pool = oracle_step(g, (args.warmup + s) * count, count)
+        total_t += dt
+        total_e += pool.examined
+    value = total_e / total_t
+    sample = (f"{count} LT RRR sets per step (of {THETA}), plus their index, plain greedy k={K} "
+              f"and RandGreedi P={PARTS}, single-threaded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2408_10982_gb300 import build, im
+    build.build_library()
+    theta = args.theta
+    first = rank * theta                         # disjoint sample ids per replica
+    g = inputs.graph_lt_scale20(SEED)
+    G = im.Graph(g)
+    cap = theta * 64
+    pool = im.Pool(G, theta, cap)
+    opts_rg = im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED, fused=True)
+    dev = torch.device("cuda", local)
+    out = dict(seeds=torch.zeros(K, dtype=torch.int32, device=dev),
+               gains=torch.zeros(K, dtype=torch.int64, device=dev),
+               ns=torch.zeros(1, dtype=torch.int32, device=dev),
+               cov=torch.zeros(1, dtype=torch.int64, device=dev))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pool.reset()
+        pool.sample(im.IM_LT, SEED, first, theta)
+        im.im_max_k_cover(pool.handle, K, None, out["seeds"], out["gains"], out["ns"],
+                          out["cov"], stream)
+        im.im_max_k_cover(pool.handle, K, opts_rg, out["seeds"], out["gains"], out["ns"],
+                          out["cov"], stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    _, total, examined = pool.info()
+    sbytes = pool.sample_bytes()
+
+    im.im_profile_reset()
+    im.im_profile_enable(True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    im.im_profile_enable(False)
+    prof = im.im_profile_read()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_step = elapsed_ms / args.steps
+    value = world * examined / (ms_step / 1000.0)
+
+    # per-kernel times (CUDA events on the launching stream, timed region)
+    per = {k: (n / args.steps, ms / args.steps) for k, (n, ms) in prof.items()}
+    launches = sum(n for n, _ in prof.values())
+    plain_ms = per.get("greedy", (0, 0))[1]
+    rg_ms = sum(v[1] for k, v in per.items() if k.startswith("randgreedi") or
+                k.startswith("partition") or k == "max_subset_size")
+    hbm, peak_kind = measured_peaks()
+    samp_name = "sample_lt"
+    samp_launch_ms = per[samp_name][1] / max(per[samp_name][0], 1)
+    achieved = sbytes / (samp_launch_ms / 1000.0) / 1e9
+    dominant = max(per.items(), key=lambda kv: kv[1][1])[0]
+    traffic = None
+    tr = TRAFFIC.get(samp_name)
+    if tr and tr["src_sha"] == src_sha("sample.cu"):
+        traffic = tr["bytes_per_launch"]
+    roofline = {"kernel": samp_name, "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "peak_kind": f"{peak_kind} hbm_gbs (copy)", "traffic": traffic,
+                "alg_bytes_per_launch": sbytes, "launch_ms": round(samp_launch_ms, 4),
+                "dominant_kernel": dominant,
+                "share": round(per[samp_name][1] / ms_step, 4)}
+
+    line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "theta_per_gpu": theta,
+                       "l2": "inputs larger than L2 (graph + LT index 277 MB, pool 1.4 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "sets_per_s": world * theta / (ms_step / 1000.0),
+            "entries_per_s": world * total / (ms_step / 1000.0),
+            "max_k_cover_ms": {"plain_greedy": round(plain_ms, 3),
+                               "randgreedi": round(rg_ms, 3)},
+            "phase_ms": {k: round(v[1], 3) for k, v in sorted(per.items())},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clk}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["bit_exact"], line["cpu_baseline"] = cpu_baseline_and_check(g, pool, first)
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, g, im, torch, dev, stream, first, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pool.close()
+    G.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline_and_check(g, pool, first):
+    """Time the oracle on a bounded sample (same graph, first ids of this
+    step) and check the GPU's sets for those ids bit for bit."""
+    import oracle as O
+    O.build()
+    count = 262144
+    dt, ref = oracle_step(g, first, count)
+    set_off, members = pool.export()
+    exact = (np.array_equal(set_off[: count + 1], ref.set_off) and
+             np.array_equal(members[: ref.set_off[-1]], ref.members))
+    sample = (f"{count} LT RRR sets (ids {first}..{first + count - 1} of {THETA}) with their "
+              f"index, plain greedy k={K} and RandGreedi P={PARTS}; single-threaded oracle")
+    return bool(exact), {"value": ref.examined / dt, "unit": "edges/s", "cores": 1,
+                         "kind": "oracle", "sample": sample, "seconds": round(dt, 2)}
+
+
+def e2e(args, g, im, torch, dev, stream, first, dist):
+    """Same metric through the C ABI from pinned host buffers, copies included."""
+    pin = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+           for k, a in (("in_off", g.in_off), ("in_src", g.in_src), ("w", g.w))}
+    res = {k: torch.zeros(sz, dtype=dt).pin_memory() for k, sz, dt in
+           (("seeds", K, torch.int32), ("gains", K, torch.int64), ("ns", 1, torch.int32),
+            ("cov", 1, torch.int64))}
+    opts_rg = im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED, fused=True)
+    steps = max(1, min(args.steps, 3))
+    examined = 0
+
+    def one():
+        nonlocal examined
+        gh = im.im_graph_create(pin["in_off"], pin["in_src"], pin["w"], g.n, g.m, stream)
+        ph = im.im_pool_create(gh, args.theta, args.theta * 64)
+        im.im_sample_rrr(gh, im.IM_LT, SEED, first, args.theta, ph, stream)
+        for o in (None, opts_rg):
+            im.im_max_k_cover(ph, K, o, res["seeds"], res["gains"], res["ns"], res["cov"], stream)
+        examined = im.im_pool_info(ph)[2]
+        im.im_pool_destroy(ph)
+        im.im_graph_destroy(gh)
+
+    one()                                   # warm-up
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    if dist:
+        t = torch.tensor([dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    world = dist.get_world_size() if dist else 1
+    h2d = 8 * (g.n + 1) + 4 * g.m + 4 * g.m
+    d2h = 2 * (4 * K + 8 * K + 4 + 8)
+    return {"value": world * examined / dt, "unit": "edges/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(1000 * dt, 3), "steps": steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -165,6 +165,31 @@ im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out
                                 int32_t *bucket_n, int32_t *bucket_seeds, int64_t *bucket_gains,
                                 int32_t *chosen, void *stream);
 
+/* Algorithmic bytes of all sampling into this pool so far -- the bytes a
+ * sampler must move, by this formula (visited-set and queue traffic is
+ * on-chip and not counted):
+ *   IC: per member 16 (its in-CSR offset pair) + 4 (member write),
+ *       per examined edge 8 (source id + weight), per set 8 (offset);
+ *   LT: per walk step at a vertex of in-degree d: 16 (offset pair)
+ *       + 8 (floor(log2 d) + 1) when d > 0 (binary search of the cumulative
+ *       weights) + 4 when an edge is picked (its source) + 4 (member write),
+ *       per set 8 (offset). */
+im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
+
+/* ---- per-kernel device timing (tracing) -------------------------------------
+ * While enabled, every kernel the library launches is bracketed by a pair of
+ * CUDA events on its stream.  im_profile_read waits for the recorded events
+ * and returns, per kernel name, the number of launches and the total device
+ * milliseconds since the last im_profile_reset:
+ *   names     char[max_entries * 48], entry i at names + 48 i, NUL-terminated
+ *   launches  int64[max_entries],  total_ms double[max_entries]
+ *   *count    number of entries written.
+ * Process-wide and thread-safe; off by default. */
+im_status im_profile_enable(int32_t on);
+im_status im_profile_reset(void);
+im_status im_profile_read(int32_t max_entries, char *names, int64_t *launches, double *total_ms,
+                          int32_t *count);
+
 /* Vertex partition of Alg. 3: part[v] = (Philox(v,0,0,4).x * P) >> 32. */
 im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
                        void *stream);

@@ -5,6 +5,8 @@
 // and CUDA errors to im_status.  No C++ exception crosses the boundary.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -39,6 +41,58 @@ im_status map_dev_status(int code, const char *where) {
             set_error(std::string(where) + ": unknown device status");
             return IM_ERR_CUDA;
     }
+}
+
+// ---- profiler -------------------------------------------------------------
+namespace {
+struct PendingTiming {
+    std::string name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<PendingTiming> g_prof_pending;
+std::map<std::string, std::pair<int64_t, double>> g_prof_acc;
+
+void prof_drain_locked() {
+    for (auto &t : g_prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&ms, t.a, t.b) ==
+                                                            cudaSuccess) {
+            auto &acc = g_prof_acc[t.name];
+            acc.first += 1;
+            acc.second += ms;
+        } else {
+            cudaGetLastError();
+        }
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    g_prof_pending.clear();
+}
+}  // namespace
+
+KernelTimer::KernelTimer(cudaStream_t st, const char *name) : st_(st), name_(name) {
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        on_ = g_prof_on;
+    }
+    if (on_) {
+        if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
+            cudaGetLastError();
+            on_ = false;
+            return;
+        }
+        cudaEventRecord(a_, st_);
+    }
+}
+
+KernelTimer::~KernelTimer() {
+    if (!on_) return;
+    cudaEventRecord(b_, st_);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.push_back({name_, a_, b_});
+    if (g_prof_pending.size() > 4096) prof_drain_locked();
 }
 
 int num_sms() {
@@ -219,7 +273,10 @@ im_status im_graph_create(const int64_t *in_off, const int32_t *in_src, const ui
     if ((e = cudaMallocAsync((void **)&d_bad, sizeof(int), st)) != cudaSuccess)
         return fail(cuda_fail(e, "im_graph_create: cudaMallocAsync"));
     cudaMemsetAsync(d_bad, 0, sizeof(int), st);
-    k_validate_graph<<<num_sms() * 4, 256, 0, st>>>(g->in_off, g->in_src, n, m, d_bad);
+    {
+        KernelTimer kt(st, "validate_graph");
+        k_validate_graph<<<num_sms() * 4, 256, 0, st>>>(g->in_off, g->in_src, n, m, d_bad);
+    }
     int bad = 0;
     cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(d_bad, st);
@@ -320,7 +377,7 @@ im_status im_pool_destroy(im_pool *p) {
 im_status im_pool_reset(im_pool *p) {
     if (!p) return IM_ERR_INVALID_ARG;
     DeviceGuard dg(p->device);
-    p->theta = p->total = p->examined = 0;
+    p->theta = p->total = p->examined = p->sample_bytes = 0;
     p->index_valid = false;
     p->pkeys_valid = false;
     IM_CUDA(cudaMemset(p->set_off, 0, 8));
@@ -456,6 +513,45 @@ im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out
     IM_TRY(copy_out(bucket_seeds, p->rg_bucket_seeds, B * k * 4, st, &host));
     IM_TRY(copy_out(bucket_gains, p->rg_bucket_gains, B * k * 8, st, &host));
     if (host) IM_CUDA(cudaStreamSynchronize(st));
+    return IM_OK;
+}
+
+im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes) {
+    if (!p || !bytes) return IM_ERR_INVALID_ARG;
+    *bytes = p->sample_bytes;
+    return IM_OK;
+}
+
+im_status im_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return IM_OK;
+}
+
+im_status im_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain_locked();
+    g_prof_acc.clear();
+    return IM_OK;
+}
+
+im_status im_profile_read(int32_t max_entries, char *names, int64_t *launches, double *total_ms,
+                          int32_t *count) {
+    if (max_entries < 0 || !count) return IM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain_locked();
+    int32_t i = 0;
+    for (auto &kv : g_prof_acc) {
+        if (i >= max_entries) break;
+        if (names) {
+            std::strncpy(names + 48 * i, kv.first.c_str(), 47);
+            names[48 * i + 47] = 0;
+        }
+        if (launches) launches[i] = kv.second.first;
+        if (total_ms) total_ms[i] = kv.second.second;
+        ++i;
+    }
+    *count = i;
     return IM_OK;
 }
 

@@ -431,6 +431,7 @@ im_status greedy_plain(im_pool *p, int32_t k, int32_t *d_seeds, int64_t *d_gains
     a.coverage = d_cov;
     a.status = d_status;
     void *args[] = {&a};
+    KernelTimer kt(st, "greedy");
     IM_CUDA(cudaLaunchCooperativeKernel((const void *)k_greedy, dim3(grid), dim3(kGreedyThreads),
                                         args, 0, st));
     return IM_OK;
@@ -573,6 +574,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
         a.nprod = std::min<int32_t>(P, resident - a.ncons);
         a.first_role = 0;
         void *args[] = {&a};
+        KernelTimer kt(st, "randgreedi_fused");
         IM_CUDA(cudaLaunchCooperativeKernel((const void *)k_randgreedi,
                                             dim3(a.nprod + a.ncons), dim3(kRGThreads), args,
                                             prod_smem, st));
@@ -581,15 +583,24 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
         a.nprod = std::min<int32_t>(P, resident);
         a.ncons = 0;
         a.first_role = 0;
-        k_randgreedi<<<a.nprod, kRGThreads, prod_smem, st>>>(a);
+        {
+            KernelTimer kt(st, "randgreedi_local");
+            k_randgreedi<<<a.nprod, kRGThreads, prod_smem, st>>>(a);
+        }
         IM_CUDA(cudaGetLastError());
         a.ncons = std::min<int32_t>(B, resident);
         a.first_role = 1;
-        k_randgreedi<<<a.ncons, kRGThreads, prod_smem, st>>>(a);
+        {
+            KernelTimer kt(st, "randgreedi_stream");
+            k_randgreedi<<<a.ncons, kRGThreads, prod_smem, st>>>(a);
+        }
         IM_CUDA(cudaGetLastError());
     }
     int32_t *d_chosen = (int32_t *)(Bs + o_l);   // l is no longer needed
-    k_rg_final<<<1, 32, 0, st>>>(a, d_seeds, d_gains, d_nseeds, d_cov, d_chosen);
+    {
+        KernelTimer kt(st, "randgreedi_final");
+        k_rg_final<<<1, 32, 0, st>>>(a, d_seeds, d_gains, d_nseeds, d_cov, d_chosen);
+    }
     IM_CUDA(cudaGetLastError());
     int32_t chosen = 0;
     IM_CUDA(cudaMemcpyAsync(&chosen, d_chosen, 4, cudaMemcpyDeviceToHost, st));

@@ -169,14 +169,20 @@ __global__ void k_max_seg(const int64_t *off, int64_t n, unsigned long long *out
 
 im_status max_segment_length(const int64_t *off, int64_t n, int64_t *d_out, cudaStream_t st) {
     IM_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int64_t), st));
-    k_max_seg<<<num_sms() * 4, 256, 0, st>>>(off, n, (unsigned long long *)d_out);
+    {
+        KernelTimer kt(st, "max_subset_size");
+        k_max_seg<<<num_sms() * 4, 256, 0, st>>>(off, n, (unsigned long long *)d_out);
+    }
     IM_CUDA(cudaGetLastError());
     return IM_OK;
 }
 
 im_status launch_partition_labels(int64_t n, int32_t P, uint64_t pseed, int32_t *part,
                                   cudaStream_t st) {
-    k_part_labels<<<num_sms() * 4, 256, 0, st>>>(n, (uint32_t)P, pseed, part);
+    {
+        KernelTimer kt(st, "partition_labels");
+        k_part_labels<<<num_sms() * 4, 256, 0, st>>>(n, (uint32_t)P, pseed, part);
+    }
     IM_CUDA(cudaGetLastError());
     return IM_OK;
 }
@@ -186,7 +192,10 @@ im_status build_index(im_pool *p, cudaStream_t st) {
     const int64_t n = p->g->n, T = p->total, theta = p->theta;
     IM_CUDA(cudaMemsetAsync(p->vtx_cursor, 0, (size_t)n * sizeof(int32_t), st));
     if (T > 0) {
-        k_vertex_hist<<<num_sms() * 8, 256, 0, st>>>(p->members, T, p->vtx_cursor);
+        {
+            KernelTimer kt(st, "index_hist");
+            k_vertex_hist<<<num_sms() * 8, 256, 0, st>>>(p->members, T, p->vtx_cursor);
+        }
         IM_CUDA(cudaGetLastError());
     }
     void *tmp = nullptr;
@@ -197,8 +206,11 @@ im_status build_index(im_pool *p, cudaStream_t st) {
     if (s != IM_OK) return s;
     IM_CUDA(cudaMemsetAsync(p->vtx_cursor, 0, (size_t)n * sizeof(int32_t), st));
     if (theta > 0) {
-        k_scatter<<<num_sms() * 8, 256, 0, st>>>(p->set_off, p->members, theta, p->vtx_off,
-                                                 p->vtx_cursor, p->set_ids);
+        {
+            KernelTimer kt(st, "index_scatter");
+            k_scatter<<<num_sms() * 8, 256, 0, st>>>(p->set_off, p->members, theta, p->vtx_off,
+                                                     p->vtx_cursor, p->set_ids);
+        }
         IM_CUDA(cudaGetLastError());
     }
     p->index_valid = true;
@@ -228,14 +240,26 @@ im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st
     s = pool_scratch(p, std::max(hist_bytes, sort_bytes), &tmp);
     if (s != IM_OK) return s;
     int32_t *hist = (int32_t *)tmp;
-    k_part_hist<<<(unsigned)nchunks, 256, (size_t)P * 4, st>>>(p->part, n, P, hist);
-    k_part_offsets<<<1, 256, 0, st>>>(hist, nchunks, P, p->part_off);
-    k_part_scatter<<<(unsigned)nchunks, 32, (size_t)P * 4, st>>>(p->part, n, P, hist,
-                                                                  p->part_off, p->part_vtx,
-                                                                  p->part_loc);
+    {
+        KernelTimer kt(st, "partition_build");
+        k_part_hist<<<(unsigned)nchunks, 256, (size_t)P * 4, st>>>(p->part, n, P, hist);
+    }
+    {
+        KernelTimer kt(st, "partition_build");
+        k_part_offsets<<<1, 256, 0, st>>>(hist, nchunks, P, p->part_off);
+    }
+    {
+        KernelTimer kt(st, "partition_build");
+        k_part_scatter<<<(unsigned)nchunks, 32, (size_t)P * 4, st>>>(p->part, n, P, hist,
+                                                                      p->part_off, p->part_vtx,
+                                                                      p->part_loc);
+    }
     IM_CUDA(cudaGetLastError());
     if (T > 0) {
-        k_part_keys<<<num_sms() * 8, 256, 0, st>>>(p->members, T, p->part, p->part_loc, p->pkeys);
+        {
+            KernelTimer kt(st, "partition_keys");
+            k_part_keys<<<num_sms() * 8, 256, 0, st>>>(p->members, T, p->part, p->part_loc, p->pkeys);
+        }
         IM_CUDA(cudaGetLastError());
         s = segmented_sort<uint64_t>(p->pkeys, p->set_off, theta, tmp, sort_bytes, st);
         if (s != IM_OK) return s;

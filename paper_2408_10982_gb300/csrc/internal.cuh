@@ -173,6 +173,7 @@ struct im_pool {
     int device;
     int64_t max_sets, max_entries;
     int64_t theta, total, examined;   // host copies, valid after every call
+    int64_t sample_bytes;             // algorithmic bytes of all sampling so far
     int64_t *set_off;                 // [max_sets+1]
     int32_t *members;                 // [max_entries]
     // covering subsets
@@ -221,6 +222,22 @@ im_status cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::im::cuda_fail(_e, #call);  \
     } while (0)
 im_status map_dev_status(int code, const char *where);
+
+// Brackets the kernels launched in its scope with timing events when the
+// profiler is on (im_profile_enable); a no-op otherwise.
+class KernelTimer {
+  public:
+    KernelTimer(cudaStream_t st, const char *name);
+    ~KernelTimer();
+    KernelTimer(const KernelTimer &) = delete;
+    KernelTimer &operator=(const KernelTimer &) = delete;
+
+  private:
+    cudaStream_t st_;
+    const char *name_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+    bool on_ = false;
+};
 
 // scratch arena of a pool: returns a pointer to at least `bytes` (256-aligned)
 im_status pool_scratch(im_pool *p, size_t bytes, void **out);

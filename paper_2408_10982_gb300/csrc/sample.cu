@@ -48,6 +48,7 @@ struct SampleArgs {
     uint32_t *gvis;
     int64_t vis_words;
     unsigned long long *examined;
+    unsigned long long *alg_bytes;
     unsigned long long *work;
     int64_t *ovf_list;
     unsigned long long *ovf_count;
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
         for (int64_t i = lane; i < a.vis_words; i += 32) vis[i] = 0;
     __syncwarp();
     const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
-    unsigned long long exam = 0;
+    unsigned long long exam = 0, abytes = 0;
     for (;;) {
         const int64_t j = next_item(a, lane);
         if (j < 0) break;
@@ -201,6 +202,8 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
         } else {
             emit_set(a, j, q, tail, lane);
             exam += sexam;
+            // 16 B offsets + 4 B write per member, 8 B per examined edge, 8 B per set
+            abytes += 8ull * sexam + (lane == 0 ? 20ull * (unsigned long long)tail + 8ull : 0ull);
         }
         // reset the visited bits of this sample
         if (tail > a.vis_words) {
@@ -214,7 +217,9 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
         __syncwarp();
     }
     exam = warp_sum<unsigned long long>(exam);
+    abytes = warp_sum<unsigned long long>(abytes);
     if (lane == 0 && exam) atomicAdd(a.examined, exam);
+    if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_lt(SampleArgs a) {
     int32_t *q = a.queues + (size_t)gw * (size_t)a.qcap;
     int32_t *sp = spath[wib];
     const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
-    unsigned long long exam = 0;
+    unsigned long long exam = 0, abytes = 0;
     for (;;) {
         const int64_t j = next_item(a, lane);
         if (j < 0) break;
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_lt(SampleArgs a) {
         __syncwarp();
         int64_t len = 1;
         bool overflow = false;
-        unsigned long long sexam = 0;
+        unsigned long long sexam = 0, sbytes = 8;
         for (;;) {
             const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
             const int64_t eb = __ldg(a.in_off + cur);
@@ -273,7 +278,12 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_lt(SampleArgs a) {
                     if (bal) pick = lo + __ffs(bal) - 1;
                 }
             }
-            if (lane == 0) sexam += (unsigned long long)(pick >= 0 ? pick + 1 : d);
+            if (lane == 0) {
+                sexam += (unsigned long long)(pick >= 0 ? pick + 1 : d);
+                // offsets, binary search of d cumulative weights, source, member write
+                sbytes += 16ull + (d > 0 ? 8ull * (64 - __clzll((unsigned long long)d)) : 0ull) +
+                          (pick >= 0 ? 4ull : 0ull) + 4ull;
+            }
             if (pick < 0) break;
             const int32_t u = __ldg(a.in_src + eb + pick);
             bool seen = false;
@@ -299,11 +309,14 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_lt(SampleArgs a) {
         } else {
             emit_set(a, j, q, len, lane);
             exam += sexam;
+            if (lane == 0) abytes += sbytes;
         }
         __syncwarp();
     }
     exam = warp_sum<unsigned long long>(exam);
+    abytes = warp_sum<unsigned long long>(abytes);
     if (lane == 0 && exam) atomicAdd(a.examined, exam);
+    if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
 }
 
 // LT cumulative weights: cdf[e] = sum of w over in-edges of dst(e) up to e.
@@ -503,7 +516,8 @@ int blocks_for(const void *kernel, int threads, size_t smem) {
 template <typename Key>
 im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, const Key *stage,
                               const int64_t *stage_off, void *tmp, size_t tmp_bytes,
-                              int64_t *ngiant_host, cudaStream_t st) {
+                              int64_t *ngiant_host, cudaStream_t st, const char *warp_name,
+                              const char *block_name) {
     // tmp layout: [2 counters][big list nseg][giant list nseg]
     if (tmp_bytes < (size_t)(2 + 2 * nseg) * 8) return IM_ERR_INVALID_ARG;
     unsigned long long *ctr = (unsigned long long *)tmp;
@@ -512,14 +526,20 @@ im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, c
     IM_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), st));
     if (nseg == 0) return IM_OK;
     const int gs = blocks_for((const void *)k_sort_small<Key>, 256, 0);
-    k_sort_small<Key><<<gs, 256, 0, st>>>(keys, seg_off, nseg, stage, stage_off, big, ctr);
+    {
+        KernelTimer kt(st, warp_name);
+        k_sort_small<Key><<<gs, 256, 0, st>>>(keys, seg_off, nseg, stage, stage_off, big, ctr);
+    }
     constexpr int kCap = sizeof(Key) == 4 ? kBlockSortCap : kSortedKeyCap64;
     static_assert(kBlockSortCap * 4 == kSortedKeyCap64 * 8, "smem sized for both key widths");
     const size_t smem = (size_t)kCap * sizeof(Key);
     IM_CUDA(cudaFuncSetAttribute(k_sort_block<Key, kCap>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sort_block<Key, kCap><<<num_sms(), 1024, smem, st>>>(keys, seg_off, big, ctr,
-                                                          giant, ctr + 1);
+    {
+        KernelTimer kt(st, block_name);
+        k_sort_block<Key, kCap><<<num_sms(), 1024, smem, st>>>(keys, seg_off, big, ctr,
+                                                              giant, ctr + 1);
+    }
     IM_CUDA(cudaGetLastError());
     if (ngiant_host) {
         unsigned long long ng = 0;
@@ -536,7 +556,8 @@ im_status segmented_sort(Key *keys, const int64_t *seg_off, int64_t nseg, void *
     // segments longer than the block cap stay as they are (callers treat them
     // as unsorted)
     return segmented_sort_impl<Key>(keys, seg_off, nseg, nullptr, nullptr, tmp, tmp_bytes,
-                                    nullptr, st);
+                                    nullptr, st, "partition_keys_sort_warp",
+                                    "partition_keys_sort_block");
 }
 template im_status segmented_sort<uint64_t>(uint64_t *, const int64_t *, int64_t, void *, size_t,
                                             cudaStream_t);
@@ -547,7 +568,10 @@ im_status build_lt_cdf(im_graph *g, cudaStream_t st) {
     int *d_invalid = nullptr;
     IM_CUDA(cudaMalloc(&d_invalid, sizeof(int)));
     IM_CUDA(cudaMemsetAsync(d_invalid, 0, sizeof(int), st));
-    k_lt_cdf<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->w, g->lt_cdf, g->n, d_invalid);
+    {
+        KernelTimer kt(st, "lt_cdf");
+        k_lt_cdf<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->w, g->lt_cdf, g->n, d_invalid);
+    }
     int invalid = 0;
     IM_CUDA(cudaMemcpyAsync(&invalid, d_invalid, sizeof(int), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaStreamSynchronize(st));
@@ -618,7 +642,8 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     if (rs != IM_OK) return rs;
     char *B = (char *)base;
     unsigned long long *ctr = (unsigned long long *)(B + o_ctr);
-    // ctr: 0 work, 1 stage cursor, 2 examined, 3 overflow count, 4 status (int)
+    // ctr: 0 work, 1 stage cursor, 2 examined, 3 overflow count, 4 status (int),
+    //      5 algorithmic bytes
     IM_CUDA(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), st));
     if (o_vis && model == IM_IC && !smem_vis)
         IM_CUDA(cudaMemsetAsync(B + o_vis, 0, (size_t)warps * vis_words * 4, st));
@@ -643,6 +668,7 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     a.gvis = (uint32_t *)(B + o_vis);
     a.vis_words = vis_words;
     a.examined = ctr + 2;
+    a.alg_bytes = ctr + 5;
     a.work = ctr;
     a.ovf_list = (int64_t *)(B + o_ovf);
     a.ovf_count = ctr + 3;
@@ -651,6 +677,7 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     pool->pkeys_valid = false;
 
     auto launch = [&](int nblocks) {
+        KernelTimer kt(st, model == IM_LT ? "sample_lt" : "sample_ic");
         if (model == IM_LT) k_sample_lt<<<nblocks, kSampleThreads, 0, st>>>(a);
         else if (smem_vis) k_sample_ic<true><<<nblocks, kSampleThreads, dyn_smem, st>>>(a);
         else k_sample_ic<false><<<nblocks, kSampleThreads, 0, st>>>(a);
@@ -658,7 +685,7 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     launch(blocks);
     IM_CUDA(cudaGetLastError());
 
-    unsigned long long hc[5];
+    unsigned long long hc[6];
     IM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaStreamSynchronize(st));
     int dev_status = (int)(hc[4] & 0xffffffffu);
@@ -711,7 +738,8 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     const int64_t gwords = vis_words;
     // giant sets (> block sort cap) need an n-bit bitmap per block
     rs = segmented_sort_impl<int32_t>(pool->members, so, cnt, a.stage, a.stage_off, B + o_sort,
-                                      (size_t)(2 + 2 * cnt) * 8, &ngiant, st);
+                                      (size_t)(2 + 2 * cnt) * 8, &ngiant, st, "sort_sets_warp",
+                                      "sort_sets_block");
     if (rs != IM_OK) return rs;
     if (ngiant > 0) {
         const int blocks3 = (int)std::min<int64_t>(ngiant, num_sms());
@@ -719,13 +747,17 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
         IM_CUDA(cudaMemsetAsync(gbm, 0, (size_t)blocks3 * gwords * 4, st));
         unsigned long long *sctr = (unsigned long long *)(B + o_sort);
         int64_t *giant = (int64_t *)(B + o_sort) + 2 + cnt;
-        k_sort_giant<<<blocks3, 1024, 0, st>>>(pool->members, so, giant, sctr + 1, gbm, gwords);
+        {
+            KernelTimer kt(st, "sort_sets_bitmap");
+            k_sort_giant<<<blocks3, 1024, 0, st>>>(pool->members, so, giant, sctr + 1, gbm, gwords);
+        }
         IM_CUDA(cudaGetLastError());
         IM_CUDA(cudaFreeAsync(gbm, st));
     }
     pool->theta += cnt;
     pool->total += added;
     pool->examined += (int64_t)hc[2];
+    pool->sample_bytes += (int64_t)hc[5];
     IM_CUDA(cudaStreamSynchronize(st));
     return IM_OK;
 }

@@ -102,13 +102,25 @@ im_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t cou
     int64_t *grand = sums + ntiles + 1;
     if (count == 0) {
         // out[0] = base
-        k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, 0, base, grand);
+        {
+            KernelTimer kt(st, "scan");
+            k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, 0, base, grand);
+        }
         IM_CUDA(cudaMemcpyAsync(out, grand, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
         return IM_OK;
     }
-    k_tile_sums<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, count, sums);
-    k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, ntiles, base, grand);
-    k_tile_scan<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, count, sums, out, grand);
+    {
+        KernelTimer kt(st, "scan");
+        k_tile_sums<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, count, sums);
+    }
+    {
+        KernelTimer kt(st, "scan");
+        k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, ntiles, base, grand);
+    }
+    {
+        KernelTimer kt(st, "scan");
+        k_tile_scan<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, count, sums, out, grand);
+    }
     IM_CUDA(cudaGetLastError());
     return IM_OK;
 }

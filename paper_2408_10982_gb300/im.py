@@ -81,6 +81,10 @@ def lib():
             "im_max_k_cover": ([vp, i32, vp, vp, vp, vp, vp, vp], ctypes.c_int),
             "im_randgreedi_details": ([vp] + [vp] * 12 + [vp], ctypes.c_int),
             "im_partition": ([i64, i32, u64, vp, vp], ctypes.c_int),
+            "im_pool_sample_bytes": ([vp, vp], ctypes.c_int),
+            "im_profile_enable": ([i32], ctypes.c_int),
+            "im_profile_reset": ([], ctypes.c_int),
+            "im_profile_read": ([i32, vp, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -222,6 +226,36 @@ def im_partition(n: int, P: int, partition_seed: int, part, stream=None):
     _check(lib().im_partition(n, P, partition_seed, _ptr(part), _stream(stream)), "im_partition")
 
 
+def im_pool_sample_bytes(p) -> int:
+    b = ctypes.c_int64()
+    _check(lib().im_pool_sample_bytes(p, ctypes.byref(b)), "im_pool_sample_bytes")
+    return b.value
+
+
+def im_profile_enable(on: bool = True):
+    _check(lib().im_profile_enable(int(on)), "im_profile_enable")
+
+
+def im_profile_reset():
+    _check(lib().im_profile_reset(), "im_profile_reset")
+
+
+def im_profile_read(max_entries: int = 64) -> dict:
+    """{kernel name: (launches, total ms)} since the last reset."""
+    names = ctypes.create_string_buffer(48 * max_entries)
+    launches = np.zeros(max_entries, np.int64)
+    ms = np.zeros(max_entries, np.float64)
+    cnt = ctypes.c_int32()
+    _check(lib().im_profile_read(max_entries, names, launches.ctypes.data, ms.ctypes.data,
+                                 ctypes.byref(cnt)), "im_profile_read")
+    raw = names.raw
+    out = {}
+    for i in range(cnt.value):
+        name = raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[name] = (int(launches[i]), float(ms[i]))
+    return out
+
+
 # --- convenience wrappers (still only marshalling) ---------------------------
 
 class Graph:
@@ -264,6 +298,12 @@ class Pool:
 
     def info(self):
         return im_pool_info(self.handle)
+
+    def sample_bytes(self) -> int:
+        return im_pool_sample_bytes(self.handle)
+
+    def reset(self):
+        im_pool_reset(self.handle)
 
     def export(self, stream=None):
         theta, total, _ = self.info()
