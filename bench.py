@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--theta", type=int, default=THETA, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--rg-fused", type=int, default=1,
+                    help="RandGreedi as one cooperative launch (1) or two launches (0)")
     return ap.parse_args()
 
 
@@ -208,7 +210,7 @@ def run_ours(args):
     G = im.Graph(g)
     cap = theta * 64
     pool = im.Pool(G, theta, cap)
-    opts_rg = im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED, fused=True)
+    opts_rg = im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED, fused=bool(args.rg_fused))
     dev = torch.device("cuda", local)
     out = dict(seeds=torch.zeros(K, dtype=torch.int32, device=dev),
                gains=torch.zeros(K, dtype=torch.int64, device=dev),

@@ -190,6 +190,13 @@ im_status im_profile_reset(void);
 im_status im_profile_read(int32_t max_entries, char *names, int64_t *launches, double *total_ms,
                           int32_t *count);
 
+/* Diagnostics of the pool's last IM_RANDGREEDI cover: int64[(P + B) * 6].
+ * Row p < P (local greedy of part p): start ns, end ns (device global timer),
+ *   rounds, lazy re-evaluations, entries scanned by re-evaluations, entries
+ *   covered.  Row P + b (bucket b): start ns, end ns, elements evaluated,
+ *   elements accepted, entries scanned, ns spent waiting for the stream. */
+im_status im_randgreedi_stats(const im_pool *p, int64_t *stats, void *stream);
+
 /* Vertex partition of Alg. 3: part[v] = (Philox(v,0,0,4).x * P) >> 32. */
 im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
                        void *stream);

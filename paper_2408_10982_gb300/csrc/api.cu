@@ -298,7 +298,9 @@ im_status im_graph_destroy(im_graph *g) {
     cudaFree(g->in_off);
     cudaFree(g->in_src);
     cudaFree(g->w);
-    cudaFree(g->lt_cdf);
+    cudaFree(g->lt_vrec);
+    cudaFree(g->lt_leaf);
+    cudaFree(g->lt_tree);
     delete g;
     return IM_OK;
 }
@@ -309,7 +311,7 @@ im_status im_graph_info(const im_graph *g, int64_t *n, int64_t *m, int32_t *lt_v
     if (n) *n = g->n;
     if (m) *m = g->m;
     if (lt_valid) {
-        if (!g->lt_cdf) IM_TRY(build_lt_cdf(const_cast<im_graph *>(g), 0));
+        if (!g->lt_leaf) IM_TRY(build_lt_index(const_cast<im_graph *>(g), 0));
         *lt_valid = g->lt_valid;
     }
     return IM_OK;
@@ -362,7 +364,6 @@ im_status im_pool_destroy(im_pool *p) {
     cudaFree(p->vtx_off);
     cudaFree(p->set_ids);
     cudaFree(p->vtx_cursor);
-    cudaFree(p->pkeys);
     cudaFree(p->part);
     cudaFree(p->part_off);
     cudaFree(p->part_vtx);
@@ -379,7 +380,6 @@ im_status im_pool_reset(im_pool *p) {
     DeviceGuard dg(p->device);
     p->theta = p->total = p->examined = p->sample_bytes = 0;
     p->index_valid = false;
-    p->pkeys_valid = false;
     IM_CUDA(cudaMemset(p->set_off, 0, 8));
     return IM_OK;
 }
@@ -512,6 +512,19 @@ im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out
     IM_TRY(copy_out(bucket_n, p->rg_bucket_n, B * 4, st, &host));
     IM_TRY(copy_out(bucket_seeds, p->rg_bucket_seeds, B * k * 4, st, &host));
     IM_TRY(copy_out(bucket_gains, p->rg_bucket_gains, B * k * 8, st, &host));
+    if (host) IM_CUDA(cudaStreamSynchronize(st));
+    return IM_OK;
+}
+
+im_status im_randgreedi_stats(const im_pool *p, int64_t *stats, void *stream) {
+    if (!p || p->rg_P == 0 || !stats) {
+        set_error("im_randgreedi_stats: no RandGreedi run on this pool");
+        return IM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(p->device);
+    cudaStream_t st = as_stream(stream);
+    bool host = false;
+    IM_TRY(copy_out(stats, p->rg_stats, (size_t)(p->rg_P + p->rg_B) * 6 * 8, st, &host));
     if (host) IM_CUDA(cudaStreamSynchronize(st));
     return IM_OK;
 }

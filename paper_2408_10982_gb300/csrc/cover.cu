@@ -10,8 +10,9 @@
 // at most kWaitLimitNs and then report IM_ERR_TIMEOUT.
 //
 // RandGreedi: the paper's m sender machines are m "producer" blocks, each
-// running the local greedy of one vertex part V_p with its gains in shared
-// memory and its own theta-bit covered bitmap; the receiver's B bucketing
+// running the lazy local greedy of one vertex part V_p (Alg. 2) with its
+// gains in shared memory and its own theta-bit covered bitmap; the receiver's
+// B bucketing
 // threads are B "consumer" blocks, one bucket each.  A producer publishes its
 // j-th seed (j < ceil(alpha k)) in slot (j, p) of a device array and raises a
 // release flag; consumers read the slots in (j, p) order with acquire loads,
@@ -31,6 +32,8 @@ namespace {
 constexpr int kGreedyThreads = 512;
 constexpr int kRGThreads = 512;
 constexpr int kBatch = 256;                  // stream slots a consumer reads at once
+constexpr int kUnroll = 8;                   // independent loads in flight per lane in scans
+constexpr int kSpec = 32;                    // largest speculative group of stream elements
 
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v,
                                                             unsigned long long *sh) {
@@ -159,8 +162,6 @@ __global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
 struct RGArgs {
     int64_t n, theta, words;
     int32_t k, P, trunc, B;
-    const int64_t *set_off;
-    const uint64_t *pkeys;
     const int64_t *vtx_off;
     const int32_t *set_ids;
     const int32_t *part_off;
@@ -180,37 +181,75 @@ struct RGArgs {
     int32_t *elems;           // [trunc][P]
     int32_t nprod, ncons;     // block roles in this launch
     int32_t first_role;       // 0: blocks start with producers; 1: consumers only
+    int32_t max_np;           // largest part: key[] and stamp[] are max_np each
+    long long *stats;         // [P + B][6] diagnostics (see im_randgreedi_stats)
     int *status;
 };
 
-// Local greedy of part p (Alg. 4, one sender): gains of V_p live in shared memory.
-__device__ void produce(const RGArgs &a, int p, int32_t *cnt, unsigned long long *shm) {
+// Local greedy of part p (Alg. 4, one sender), run as the lazy greedy of
+// Alg. 2: key[l] holds a gain of candidate l that is exact when stamp[l]
+// equals the current round and an upper bound otherwise (gains only shrink,
+// by submodularity).  A round takes the largest key (ties: smallest id); a
+// fresh winner is the true argmax and is taken, a stale one is re-evaluated
+// against the partition's covered bitmap and the round retried.  This picks
+// exactly the standard greedy's sequence, and needs no member lists of R(i).
+__device__ void produce(const RGArgs &a, int p, int32_t *key, unsigned long long *shm,
+                        long long *shs) {
     const int32_t vb = a.part_off[p], np = a.part_off[p + 1] - vb;
     const int32_t *vtx = a.part_vtx + vb;
+    int32_t *stamp = key + a.max_np;
     uint32_t *cov = a.covered + (size_t)p * (size_t)a.words;
     for (int64_t x = threadIdx.x; x < a.words; x += blockDim.x) cov[x] = 0u;
     for (int32_t l = threadIdx.x; l < np; l += blockDim.x) {
         const int32_t v = vtx[l];
-        cnt[l] = (int32_t)(a.vtx_off[v + 1] - a.vtx_off[v]);
+        key[l] = (int32_t)(a.vtx_off[v + 1] - a.vtx_off[v]);
+        stamp[l] = 0;                                   // exact: nothing is covered yet
     }
     __syncthreads();
-    const uint64_t lo_key = (uint64_t)(uint32_t)p << 32, hi_key = (uint64_t)(uint32_t)(p + 1) << 32;
+    const uint64_t t_begin = global_ns();
+    long long n_rounds = 0, n_evals = 0, eval_entries = 0, cover_entries = 0;
     int64_t total = 0;
     int32_t j = 0;
-    for (; j < a.k; ++j) {
+    while (j < a.k) {
+        ++n_rounds;
         unsigned long long best = 0;
         for (int32_t l = threadIdx.x; l < np; l += blockDim.x) {
-            const int32_t c = cnt[l];
+            const int32_t c = key[l];
             if (c > 0) {
-                const unsigned long long key =
+                const unsigned long long kk =
                     ((unsigned long long)(uint32_t)c << 32) | (0xffffffffu - (uint32_t)l);
-                best = key > best ? key : best;
+                best = kk > best ? kk : best;
             }
         }
         best = block_max_u64(best, shm);
-        if (best == 0) break;
+        if (best == 0) break;                           // every gain is zero
         const int32_t l = (int32_t)(0xffffffffu - (uint32_t)(best & 0xffffffffu));
         const int32_t v = vtx[l];
+        const int64_t sb = a.vtx_off[v], se = a.vtx_off[v + 1];
+        if (stamp[l] != j) {
+            // stale: recompute |S(v) \ covered| and retry the round
+            long long miss = 0;
+            for (int64_t t0 = sb + threadIdx.x; t0 < se; t0 += (int64_t)blockDim.x * kUnroll) {
+                int32_t ids[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int64_t t = t0 + (int64_t)u * blockDim.x;
+                    ids[u] = t < se ? __ldg(a.set_ids + t) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u)
+                    if (ids[u] >= 0) miss += !((__ldcg(cov + (ids[u] >> 5)) >> (ids[u] & 31)) & 1u);
+            }
+            const long long g = block_sum_i64(miss, shs);
+            if (threadIdx.x == 0) {
+                key[l] = (int32_t)g;
+                stamp[l] = j;
+            }
+            ++n_evals;
+            eval_entries += se - sb;
+            __syncthreads();
+            continue;
+        }
         const int64_t gain = (int64_t)(best >> 32);
         if (threadIdx.x == 0) {
             a.local_seeds[(int64_t)p * a.k + j] = v;
@@ -219,60 +258,65 @@ __device__ void produce(const RGArgs &a, int p, int32_t *cnt, unsigned long long
                 a.elems[(int64_t)j * a.P + p] = v;
                 st_release_u32(&a.flags[(int64_t)j * a.P + p], 1u);
             }
+            key[l] = 0;
         }
         total += gain;
-        const int64_t sb = a.vtx_off[v], se = a.vtx_off[v + 1];
+        cover_entries += se - sb;
         for (int64_t t = sb + threadIdx.x; t < se; t += blockDim.x) {
             const int32_t i = a.set_ids[t];
-            const uint32_t bit = 1u << (i & 31);
-            if (atomicOr(&cov[i >> 5], bit) & bit) continue;
-            // members of R(i) in V_p: keys in [lo_key, hi_key)
-            const int64_t so = a.set_off[i], eo = a.set_off[i + 1];
-            if (eo - so <= kSortedKeyCap64) {
-                int64_t lo = so, hi = eo;
-                while (lo < hi) {
-                    const int64_t mid = (lo + hi) >> 1;
-                    if (a.pkeys[mid] < lo_key) lo = mid + 1;
-                    else hi = mid;
-                }
-                for (int64_t q = lo; q < eo; ++q) {
-                    const uint64_t key = a.pkeys[q];
-                    if (key >= hi_key) break;
-                    atomicSub(&cnt[(uint32_t)key], 1);
-                }
-            } else {
-                for (int64_t q = so; q < eo; ++q) {
-                    const uint64_t key = a.pkeys[q];
-                    if (key >= lo_key && key < hi_key) atomicSub(&cnt[(uint32_t)key], 1);
-                }
-            }
+            atomicOr(&cov[i >> 5], 1u << (i & 31));
         }
         __syncthreads();
+        ++j;
     }
     if (threadIdx.x == 0) {
         a.local_n[p] = j;
         a.local_cov[p] = total;
         for (int32_t jj = j; jj < a.trunc; ++jj) st_release_u32(&a.flags[(int64_t)jj * a.P + p], 2u);
+        if (a.stats) {
+            long long *st = a.stats + 6 * (int64_t)p;
+            st[0] = (long long)t_begin;
+            st[1] = (long long)global_ns();
+            st[2] = n_rounds;
+            st[3] = n_evals;
+            st[4] = eval_entries;
+            st[5] = cover_entries;
+        }
     }
     __syncthreads();
 }
 
 // Streaming bucket b (Alg. 5): consume the stream in (j, p) order.
+//
+// Elements are evaluated speculatively in groups of W against the bucket as
+// it stands: the first element of the group whose gain reaches the threshold
+// is the next one the sequential rule accepts (every element before it saw
+// the same bucket and fell short), so it is accepted and evaluation resumes
+// right after it; later elements of the group are evaluated again.  W doubles
+// after a group without an accept and halves after one, which bounds the
+// repeated work by the number of accepts times W.
 __device__ void consume(const RGArgs &a, int b, long long *shs) {
     __shared__ int32_t s_x[kBatch];
     __shared__ int64_t s_off[kBatch];
     __shared__ int64_t s_len[kBatch];
-    __shared__ int s_timeout;
+    __shared__ int s_cand[kSpec];
+    __shared__ unsigned long long s_miss[kSpec];
+    __shared__ int s_ncand, s_end, s_acc, s_timeout;
     uint32_t *C = a.bcovered + (size_t)b * (size_t)a.words;
     for (int64_t x = threadIdx.x; x < a.words; x += blockDim.x) C[x] = 0u;
     if (threadIdx.x == 0) s_timeout = 0;
     __syncthreads();
     const int64_t T = a.thr[b];
     const int64_t E = (int64_t)a.trunc * a.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint64_t t_begin = global_ns();
+    long long n_eval = 0, scanned = 0, wait_ns = 0;
     int32_t bn = 0;
     int64_t bcov = 0;
+    int W = 1;
     for (int64_t base = 0; base < E && bn < a.k; base += kBatch) {
-        const int64_t cntb = min((int64_t)kBatch, E - base);
+        const int cntb = (int)min((int64_t)kBatch, E - base);
+        const uint64_t tw0 = global_ns();
         if (threadIdx.x < cntb) {
             const int64_t slot = base + threadIdx.x;
             uint32_t f = ld_acquire_u32(a.flags + slot);
@@ -299,50 +343,115 @@ __device__ void consume(const RGArgs &a, int b, long long *shs) {
             s_len[threadIdx.x] = len;
         }
         __syncthreads();
+        wait_ns += (long long)(global_ns() - tw0);
         if (s_timeout) break;
-        for (int64_t q = 0; q < cntb && bn < a.k; ++q) {
-            const int32_t x = s_x[q];
-            const int64_t len = s_len[q];
-            if (x < 0 || len < T) continue;      // |S(x) \ C_b| <= |S(x)| < threshold
-            const int64_t off = s_off[q];
-            long long miss = 0;
-            for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
-                const int32_t i = a.set_ids[off + t];
-                miss += !((__ldcg(C + (i >> 5)) >> (i & 31)) & 1u);
+        int q = 0;
+        while (q < cntb && bn < a.k) {
+            if (threadIdx.x == 0) {
+                // next W candidates; |S(x)| < threshold rejects x without a scan
+                int n = 0, r = q;
+                while (r < cntb && n < W) {
+                    if (s_x[r] >= 0 && s_len[r] >= T) s_cand[n++] = r;
+                    ++r;
+                }
+                s_ncand = n;
+                s_end = r;
             }
-            const long long gain = block_sum_i64(miss, shs);
-            if (gain >= T) {
+            if (threadIdx.x < kSpec) s_miss[threadIdx.x] = 0;
+            __syncthreads();
+            const int n = s_ncand;
+            if (n == 0) {
+                q = s_end;
+                __syncthreads();
+                continue;
+            }
+            // |S(x) \ C_b| for every candidate, all warps in flight at once
+            for (int c = 0; c < n; ++c) {
+                const int r = s_cand[c];
+                const int64_t off = s_off[r], len = s_len[r];
+                unsigned m = 0;
+                for (int64_t c0 = (int64_t)warp * 32 * kUnroll; c0 < len;
+                     c0 += (int64_t)nwarps * 32 * kUnroll) {
+                    int32_t ids[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int64_t t = c0 + u * 32 + lane;
+                        ids[u] = t < len ? __ldg(a.set_ids + off + t) : -1;
+                    }
+                    unsigned words[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u)
+                        words[u] = ids[u] >= 0 ? __ldcg(C + (ids[u] >> 5)) : ~0u;
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u)
+                        m += __popc(__ballot_sync(kFull, !((words[u] >> (ids[u] & 31)) & 1u)));
+                }
+                if (lane == 0 && m) atomicAdd(&s_miss[c], (unsigned long long)m);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int acc = -1;
+                for (int c = 0; c < n; ++c)
+                    if ((int64_t)s_miss[c] >= T) {
+                        acc = c;
+                        break;
+                    }
+                s_acc = acc;
+            }
+            __syncthreads();
+            const int acc = s_acc;
+            n_eval += acc < 0 ? n : acc + 1;
+            for (int c = 0; c < n; ++c) scanned += s_len[s_cand[c]];
+            if (acc < 0) {
+                q = s_end;
+                W = min(kSpec, 2 * W);
+            } else {
+                const int r = s_cand[acc];
+                const int64_t off = s_off[r], len = s_len[r];
                 for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
-                    const int32_t i = a.set_ids[off + t];
+                    const int32_t i = __ldg(a.set_ids + off + t);
                     atomicOr(&C[i >> 5], 1u << (i & 31));
                 }
+                const int64_t gain = (int64_t)s_miss[acc];
                 if (threadIdx.x == 0) {
-                    a.bucket_seeds[(int64_t)b * a.k + bn] = x;
+                    a.bucket_seeds[(int64_t)b * a.k + bn] = s_x[r];
                     a.bucket_gains[(int64_t)b * a.k + bn] = gain;
                 }
                 ++bn;
                 bcov += gain;
-                __syncthreads();
+                q = r + 1;
+                W = max(1, W / 2);
             }
+            __syncthreads();
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         a.bucket_n[b] = bn;
         a.bucket_cov[b] = bcov;
+        if (a.stats) {
+            long long *st = a.stats + 6 * ((int64_t)a.P + b);
+            st[0] = (long long)t_begin;
+            st[1] = (long long)global_ns();
+            st[2] = n_eval;
+            st[3] = bn;
+            st[4] = scanned;
+            st[5] = wait_ns;
+        }
     }
     __syncthreads();
 }
 
 __global__ void __launch_bounds__(kRGThreads) k_randgreedi(RGArgs a) {
-    extern __shared__ int32_t cnt[];
+    extern __shared__ int32_t key[];
     __shared__ unsigned long long shm[33];
+    __shared__ long long shs[33];
     const int r = blockIdx.x;
     if (a.first_role == 0 && r < a.nprod) {
-        for (int p = r; p < a.P; p += a.nprod) produce(a, p, cnt, shm);
+        for (int p = r; p < a.P; p += a.nprod) produce(a, p, key, shm, shs);
     } else {
         const int c = a.first_role == 0 ? r - a.nprod : r;
-        for (int b = c; b < a.B; b += a.ncons) consume(a, b, (long long *)shm);
+        for (int b = c; b < a.B; b += a.ncons) consume(a, b, shs);
     }
 }
 
@@ -457,7 +566,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     IM_CUDA(cudaStreamSynchronize(st));
     int32_t max_np = 0;
     for (int q = 0; q < P; ++q) max_np = std::max(max_np, hoff[q + 1] - hoff[q]);
-    const size_t prod_smem = (size_t)std::max(max_np, 1) * 4;
+    const size_t prod_smem = (size_t)std::max(max_np, 1) * 8;   // key + stamp
     if (prod_smem > 200 * 1024) {
         set_error("RandGreedi: a vertex part is too large for shared memory; use more partitions");
         return IM_ERR_UNSUPPORTED;
@@ -467,7 +576,8 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     const size_t need = align256((size_t)P * k * 4) + align256((size_t)P * k * 8) +
                         align256((size_t)P * 4) + align256((size_t)P * 8) +
                         align256((size_t)B * 8) * 2 + align256((size_t)B * 4) +
-                        align256((size_t)B * k * 4) + align256((size_t)B * k * 8);
+                        align256((size_t)B * k * 4) + align256((size_t)B * k * 8) +
+                        align256((size_t)(P + B) * 6 * 8);
     if (p->rg_cap_bytes < need) {
         if (p->rg_block) cudaFree(p->rg_block);
         p->rg_block = nullptr;
@@ -492,6 +602,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
         p->rg_bucket_n = (int32_t *)grab((size_t)B * 4);
         p->rg_bucket_seeds = (int32_t *)grab((size_t)B * k * 4);
         p->rg_bucket_gains = (int64_t *)grab((size_t)B * k * 8);
+        p->rg_stats = (long long *)grab((size_t)(P + B) * 6 * 8);
     }
     p->rg_P = P;
     p->rg_B = B;
@@ -540,8 +651,6 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     a.P = P;
     a.trunc = trunc;
     a.B = B;
-    a.set_off = p->set_off;
-    a.pkeys = p->pkeys;
     a.vtx_off = p->vtx_off;
     a.set_ids = p->set_ids;
     a.part_off = p->part_off;
@@ -560,6 +669,8 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     a.flags = (uint32_t *)(Bs + o_flags);
     a.elems = (int32_t *)(Bs + o_elems);
     a.status = d_status;
+    a.max_np = std::max(max_np, 1);
+    a.stats = p->rg_stats;
 
     IM_CUDA(cudaFuncSetAttribute(k_randgreedi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)prod_smem));

@@ -7,10 +7,9 @@
 // Set ids inside one S(v) land in atomic order; nothing downstream depends on
 // that order.
 //
-// For RandGreedi every vertex gets a Philox label part(v) in [0, P) and a
-// local index loc(v) = its rank among the vertices of its part (ascending id).
-// Each RRR set's members are then re-keyed as (part << 32 | loc) and sorted,
-// so that R(i) restricted to V_p is one contiguous run found by binary search.
+// For RandGreedi every vertex gets a Philox label part(v) in [0, P); the
+// vertices of each part are listed in ascending id (part_off / part_vtx), and
+// loc(v) is v's rank inside its part.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -145,15 +144,6 @@ __global__ void k_part_scatter(const int32_t *part, int64_t n, int32_t P, const 
     }
 }
 
-__global__ void k_part_keys(const int32_t *members, int64_t T, const int32_t *part,
-                            const int32_t *part_loc, uint64_t *keys) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t u = members[t];
-        keys[t] = ((uint64_t)(uint32_t)part[u] << 32) | (uint32_t)part_loc[u];
-    }
-}
-
 __global__ void k_max_seg(const int64_t *off, int64_t n, unsigned long long *out) {
     unsigned long long m = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -218,8 +208,8 @@ im_status build_index(im_pool *p, cudaStream_t st) {
 }
 
 im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st) {
-    if (p->pkeys_valid && p->pkeys_P == P && p->pkeys_seed == pseed) return IM_OK;
-    const int64_t n = p->g->n, T = p->total, theta = p->theta;
+    if (p->part_valid && p->part_P == P && p->part_seed == pseed) return IM_OK;
+    const int64_t n = p->g->n;
     if (!p->part) {
         IM_CUDA(cudaMalloc(&p->part, (size_t)n * 4));
         IM_CUDA(cudaMalloc(&p->part_vtx, (size_t)n * 4));
@@ -230,43 +220,26 @@ im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st
         IM_CUDA(cudaMalloc(&p->part_off, (size_t)(P + 1) * 4));
         p->part_cap = P;
     }
-    if (!p->pkeys) IM_CUDA(cudaMalloc(&p->pkeys, (size_t)std::max<int64_t>(1, p->max_entries) * 8));
     im_status s = launch_partition_labels(n, P, pseed, p->part, st);
     if (s != IM_OK) return s;
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
     const size_t hist_bytes = (size_t)nchunks * P * 4;
-    const size_t sort_bytes = (size_t)(2 + 2 * std::max<int64_t>(theta, 1)) * 8;
     void *tmp = nullptr;
-    s = pool_scratch(p, std::max(hist_bytes, sort_bytes), &tmp);
+    s = pool_scratch(p, hist_bytes, &tmp);
     if (s != IM_OK) return s;
     int32_t *hist = (int32_t *)tmp;
     {
         KernelTimer kt(st, "partition_build");
         k_part_hist<<<(unsigned)nchunks, 256, (size_t)P * 4, st>>>(p->part, n, P, hist);
-    }
-    {
-        KernelTimer kt(st, "partition_build");
         k_part_offsets<<<1, 256, 0, st>>>(hist, nchunks, P, p->part_off);
-    }
-    {
-        KernelTimer kt(st, "partition_build");
         k_part_scatter<<<(unsigned)nchunks, 32, (size_t)P * 4, st>>>(p->part, n, P, hist,
                                                                       p->part_off, p->part_vtx,
                                                                       p->part_loc);
     }
     IM_CUDA(cudaGetLastError());
-    if (T > 0) {
-        {
-            KernelTimer kt(st, "partition_keys");
-            k_part_keys<<<num_sms() * 8, 256, 0, st>>>(p->members, T, p->part, p->part_loc, p->pkeys);
-        }
-        IM_CUDA(cudaGetLastError());
-        s = segmented_sort<uint64_t>(p->pkeys, p->set_off, theta, tmp, sort_bytes, st);
-        if (s != IM_OK) return s;
-    }
-    p->pkeys_valid = true;
-    p->pkeys_P = P;
-    p->pkeys_seed = pseed;
+    p->part_valid = true;
+    p->part_P = P;
+    p->part_seed = pseed;
     return IM_OK;
 }
 

@@ -75,10 +75,6 @@ constexpr int kDevBadInput = 4;
 
 __device__ __forceinline__ void raise_status(int *status, int code) { atomicCAS(status, 0, code); }
 
-// Segments longer than this many 64-bit keys are left unsorted by the
-// segmented sort (their readers scan them linearly).
-constexpr int kSortedKeyCap64 = 8192;
-
 // Every device spin-wait gives up after this many nanoseconds.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
@@ -163,7 +159,11 @@ struct im_graph {
     int64_t *in_off;     // [n+1]
     int32_t *in_src;     // [m]
     uint32_t *w;         // [m], 16-byte aligned
-    uint64_t *lt_cdf;    // [m] per-vertex inclusive running sums of w (LT), lazily built
+    // LT search index, built on first LT use: per-vertex records, per-edge
+    // leaves (running weight sum << 31 | source) and upper tree levels
+    uint4 *lt_vrec;                  // [n] {edge offset, in-degree, tree offset, 0}
+    unsigned long long *lt_leaf;     // [m]
+    unsigned long long *lt_tree;     // [sum over vertices of the upper-level sizes]
     int32_t lt_valid;
     int64_t max_indeg;
 };
@@ -181,11 +181,10 @@ struct im_pool {
     int64_t *vtx_off;                 // [n+1]
     int32_t *set_ids;                 // [max_entries]; also the sampling stage
     int32_t *vtx_cursor;              // [n] scratch
-    // RandGreedi partition-grouped member keys (part << 32 | local index)
-    uint64_t *pkeys;                  // [max_entries], lazily allocated
-    int32_t pkeys_P;                  // partition count / seed the keys were built for
-    uint64_t pkeys_seed;
-    bool pkeys_valid;
+    // RandGreedi vertex partition (labels, per-part ascending vertex lists)
+    int32_t part_P;                   // partition count / seed the lists were built for
+    uint64_t part_seed;
+    bool part_valid;
     int32_t *part;                    // [n]
     int32_t *part_off;                // [P+1]
     int32_t *part_vtx;                // [n]
@@ -202,6 +201,7 @@ struct im_pool {
     int32_t *rg_bucket_n;             // [B]
     int32_t *rg_bucket_seeds;         // [B*k]
     int64_t *rg_bucket_gains;         // [B*k]
+    long long *rg_stats;              // [(P+B)*6] diagnostics
     size_t rg_cap_bytes;
     void *rg_block;
     // scratch arena (grown on demand) and per-call results
@@ -253,10 +253,7 @@ size_t scan_tmp_bytes(int64_t count);
 // sample.cu
 im_status sample_append(const im_graph *g, im_model model, uint64_t seed, uint64_t first,
                         uint64_t count, im_pool *pool, cudaStream_t st);
-im_status build_lt_cdf(im_graph *g, cudaStream_t st);
-template <typename Key>
-im_status segmented_sort(Key *keys, const int64_t *seg_off, int64_t nseg, void *tmp,
-                         size_t tmp_bytes, cudaStream_t st);
+im_status build_lt_index(im_graph *g, cudaStream_t st);
 
 // index.cu
 im_status build_index(im_pool *p, cudaStream_t st);

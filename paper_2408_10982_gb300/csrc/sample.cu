@@ -33,7 +33,9 @@ struct SampleArgs {
     const int64_t *in_off;
     const int32_t *in_src;
     const uint32_t *w;
-    const uint64_t *cdf;
+    const uint4 *lt_vrec;             // per vertex {edge offset, in-degree, tree offset, 0}
+    const unsigned long long *lt_leaf;  // per edge: cumulative weight << 31 | source
+    const unsigned long long *lt_tree;  // per vertex: upper levels of the search tree
     uint64_t seed;
     uint32_t first;
     int64_t count;            // work items
@@ -226,8 +228,23 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
 // LT: backward walk of the LT live-edge world.  Vertex v picks the first
 // in-edge whose running weight sum exceeds Philox(s, v, 0, pick tag).x; the
 // walk stops when nothing is picked or the picked source is already on it.
+//
+// The pick is found in a fanout-32 search tree over v's running sums (built
+// by k_lt_index): every level is read as one contiguous window of at most 32
+// values, one per lane, and a ballot selects the child -- so a step costs
+// ceil(log32 d) + 1 coalesced loads instead of scattered probes, and the leaf
+// that matches also carries the source id.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSampleThreads) k_sample_lt(SampleArgs a) {
+__device__ __forceinline__ int lt_levels(int64_t d) {
+    int L = 0;
+    while (d > 32) {
+        d = (d + 31) >> 5;
+        ++L;
+    }
+    return L;
+}
+
+__global__ void __launch_bounds__(kSampleThreads, 8) k_sample_lt(SampleArgs a) {
     __shared__ int32_t spath[kWarps][kPathSmem];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wib;
@@ -245,51 +262,63 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_lt(SampleArgs a) {
             sp[0] = (int32_t)cur;
         }
         __syncwarp();
-        int64_t len = 1;
+        int32_t len = 1;
         bool overflow = false;
-        unsigned long long sexam = 0, sbytes = 8;
+        unsigned long long sexam = 0;
+        uint32_t sbytes = 8;   // flushed into abytes before it can wrap
         for (;;) {
             const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
-            const int64_t eb = __ldg(a.in_off + cur);
-            const int64_t d = __ldg(a.in_off + cur + 1) - eb;
+            const unsigned long long xs = (unsigned long long)x;
+            const uint4 vr = __ldg(a.lt_vrec + cur);
+            const int64_t eb = vr.x, d = vr.y;
             int64_t pick = -1;
+            unsigned long long leaf = 0;
             if (d > 0) {
-                int64_t lo = 0, hi = d;
+                const int L = lt_levels(d);
+                const unsigned long long *lvl = a.lt_tree + vr.z;   // levels stored top-down
+                int64_t blk = 0;
                 bool none = false;
-                while (hi - lo > 32) {
-                    const int64_t step = (hi - lo + 31) >> 5;
-                    int64_t probe = lo + (int64_t)(lane + 1) * step - 1;
-                    if (probe > hi - 1) probe = hi - 1;
-                    const bool pr = (uint64_t)x < __ldg(a.cdf + eb + probe);
+                for (int l = L; l >= 1; --l) {
+                    const int64_t sz = (d + (1ll << (5 * l)) - 1) >> (5 * l);
+                    const int64_t idx = blk * 32 + lane;
+                    const bool pr = idx < sz && xs < __ldg(lvl + idx);
                     const unsigned bal = __ballot_sync(kFull, pr);
                     if (!bal) {
                         none = true;
                         break;
                     }
-                    const int f = __ffs(bal) - 1;
-                    const int64_t nlo = lo + (int64_t)f * step;
-                    hi = min(lo + (int64_t)(f + 1) * step, hi);
-                    lo = nlo;
+                    blk = blk * 32 + (__ffs(bal) - 1);
+                    lvl += sz;
                 }
                 if (!none) {
-                    const int64_t idx = lo + lane;
-                    const bool pr = idx < hi && (uint64_t)x < __ldg(a.cdf + eb + idx);
+                    const int64_t idx = blk * 32 + lane;
+                    unsigned long long r = 0;
+                    if (idx < d) r = __ldg(a.lt_leaf + eb + idx);
+                    const bool pr = idx < d && xs < (r >> 31);
                     const unsigned bal = __ballot_sync(kFull, pr);
-                    if (bal) pick = lo + __ffs(bal) - 1;
+                    if (bal) {
+                        const int f = __ffs(bal) - 1;
+                        pick = blk * 32 + f;
+                        leaf = __shfl_sync(kFull, r, f);
+                    }
                 }
             }
             if (lane == 0) {
                 sexam += (unsigned long long)(pick >= 0 ? pick + 1 : d);
                 // offsets, binary search of d cumulative weights, source, member write
-                sbytes += 16ull + (d > 0 ? 8ull * (64 - __clzll((unsigned long long)d)) : 0ull) +
-                          (pick >= 0 ? 4ull : 0ull) + 4ull;
+                sbytes += 16u + (d > 0 ? 8u * (uint32_t)(32 - __clz((uint32_t)d)) : 0u) +
+                          (pick >= 0 ? 4u : 0u) + 4u;
+                if (sbytes > (1u << 30)) {   // only long walks of the second pass get here
+                    abytes += sbytes;
+                    sbytes = 0;
+                }
             }
             if (pick < 0) break;
-            const int32_t u = __ldg(a.in_src + eb + pick);
+            const int32_t u = (int32_t)(leaf & 0x7fffffffull);
             bool seen = false;
-            const int64_t ls = len < kPathSmem ? len : kPathSmem;
-            for (int64_t i = lane; i < ls; i += 32) seen |= sp[i] == u;
-            for (int64_t i = kPathSmem + lane; i < len; i += 32) seen |= q[i] == u;
+            const int32_t ls = len < kPathSmem ? len : kPathSmem;
+            for (int32_t i = lane; i < ls; i += 32) seen |= sp[i] == u;
+            for (int32_t i = kPathSmem + lane; i < len; i += 32) seen |= q[i] == u;
             if (__any_sync(kFull, seen)) break;
             if (len >= a.qcap) {
                 overflow = true;
@@ -319,23 +348,59 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_lt(SampleArgs a) {
     if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
 }
 
-// LT cumulative weights: cdf[e] = sum of w over in-edges of dst(e) up to e.
-__global__ void k_lt_cdf(const int64_t *in_off, const uint32_t *w, uint64_t *cdf, int64_t n,
-                         int *invalid) {
+// LT search index.  For vertex v with in-edges [eb, eb + d):
+//   leaf[e] = (sum of w over v's in-edges up to and including e) << 31 | src(e)
+// (the running sum is at most 2^32 for valid LT weights -- 33 bits -- and
+// source ids stay below 2^31, so the pair packs into 64 bits), and for
+// d > 32 the upper levels l = L .. 1 of a fanout-32 tree, stored top-down at
+// tree[tree_off(v) ..]: level l has ceil(d / 32^l) entries, entry i being the
+// running sum at the last leaf of its 32^l-leaf block.
+__device__ __forceinline__ int64_t lt_tree_size(int64_t d) {
+    int64_t total = 0;
+    while (d > 32) {
+        d = (d + 31) >> 5;
+        total += d;
+    }
+    return total;
+}
+
+__global__ void k_lt_tree_sizes(const int64_t *in_off, int64_t n, int32_t *sizes) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        sizes[v] = (int32_t)lt_tree_size(in_off[v + 1] - in_off[v]);
+}
+
+__global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const uint32_t *w,
+                           const int64_t *tree_off, unsigned long long *leaf,
+                           unsigned long long *tree, uint4 *vrec, int64_t n, int *invalid) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
          v += nw) {
-        const int64_t b = in_off[v], e = in_off[v + 1];
-        uint64_t carry = 0;
+        const int64_t b = in_off[v], e = in_off[v + 1], d = e - b;
+        unsigned long long carry = 0;
         for (int64_t base = b; base < e; base += 32) {
             const int64_t i = base + lane;
-            const uint64_t x = i < e ? (uint64_t)w[i] : 0ull;
-            const uint64_t incl = warp_incl_scan<unsigned long long>(x, lane);
-            if (i < e) cdf[i] = carry + incl;
+            const unsigned long long x = i < e ? (unsigned long long)w[i] : 0ull;
+            const unsigned long long incl = warp_incl_scan<unsigned long long>(x, lane);
+            if (i < e) leaf[i] = ((carry + incl) << 31) | (unsigned long long)(uint32_t)in_src[i];
             carry += __shfl_sync(kFull, incl, 31);
         }
         if (lane == 0 && carry > (1ull << 32)) atomicExch(invalid, 1);
+        if (lane == 0) vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], 0u);
+        __syncwarp();
+        // upper levels, top-down
+        int L = 0;
+        for (int64_t t = d; t > 32; t = (t + 31) >> 5) ++L;
+        unsigned long long *lvl = tree + tree_off[v];
+        for (int l = L; l >= 1; --l) {
+            const int64_t sz = (d + (1ll << (5 * l)) - 1) >> (5 * l);
+            for (int64_t i = lane; i < sz; i += 32) {
+                const int64_t last = min((i + 1) << (5 * l), d) - 1;
+                lvl[i] = leaf[b + last] >> 31;
+            }
+            lvl += sz;
+        }
     }
 }
 
@@ -346,8 +411,6 @@ template <typename Key>
 __device__ __forceinline__ Key key_max();
 template <>
 __device__ __forceinline__ int32_t key_max<int32_t>() { return 0x7fffffff; }
-template <>
-__device__ __forceinline__ uint64_t key_max<uint64_t>() { return ~0ull; }
 
 template <typename Key>
 __device__ __forceinline__ Key warp_bitonic32(Key v, int lane) {
@@ -530,8 +593,7 @@ im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, c
         KernelTimer kt(st, warp_name);
         k_sort_small<Key><<<gs, 256, 0, st>>>(keys, seg_off, nseg, stage, stage_off, big, ctr);
     }
-    constexpr int kCap = sizeof(Key) == 4 ? kBlockSortCap : kSortedKeyCap64;
-    static_assert(kBlockSortCap * 4 == kSortedKeyCap64 * 8, "smem sized for both key widths");
+    constexpr int kCap = kBlockSortCap * 4 / (int)sizeof(Key);
     const size_t smem = (size_t)kCap * sizeof(Key);
     IM_CUDA(cudaFuncSetAttribute(k_sort_block<Key, kCap>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -550,32 +612,42 @@ im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, c
     return IM_OK;
 }
 
-template <typename Key>
-im_status segmented_sort(Key *keys, const int64_t *seg_off, int64_t nseg, void *tmp,
-                         size_t tmp_bytes, cudaStream_t st) {
-    // segments longer than the block cap stay as they are (callers treat them
-    // as unsorted)
-    return segmented_sort_impl<Key>(keys, seg_off, nseg, nullptr, nullptr, tmp, tmp_bytes,
-                                    nullptr, st, "partition_keys_sort_warp",
-                                    "partition_keys_sort_block");
-}
-template im_status segmented_sort<uint64_t>(uint64_t *, const int64_t *, int64_t, void *, size_t,
-                                            cudaStream_t);
-
-im_status build_lt_cdf(im_graph *g, cudaStream_t st) {
-    if (g->lt_cdf) return IM_OK;
-    IM_CUDA(cudaMalloc(&g->lt_cdf, (size_t)std::max<int64_t>(g->m, 1) * sizeof(uint64_t)));
+im_status build_lt_index(im_graph *g, cudaStream_t st) {
+    if (g->lt_leaf) return IM_OK;
+    const int64_t n = g->n, m = g->m;
+    int32_t *sizes = nullptr;
+    int64_t *toff = nullptr;
     int *d_invalid = nullptr;
-    IM_CUDA(cudaMalloc(&d_invalid, sizeof(int)));
+    IM_CUDA(cudaMallocAsync((void **)&sizes, (size_t)n * 4, st));
+    IM_CUDA(cudaMallocAsync((void **)&toff, (size_t)(n + 1) * 8 + scan_tmp_bytes(n) + 256, st));
+    IM_CUDA(cudaMallocAsync((void **)&d_invalid, sizeof(int), st));
     IM_CUDA(cudaMemsetAsync(d_invalid, 0, sizeof(int), st));
     {
-        KernelTimer kt(st, "lt_cdf");
-        k_lt_cdf<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->w, g->lt_cdf, g->n, d_invalid);
+        KernelTimer kt(st, "lt_index");
+        k_lt_tree_sizes<<<num_sms() * 4, 256, 0, st>>>(g->in_off, n, sizes);
     }
+    void *scan_tmp = (char *)toff + (((size_t)(n + 1) * 8 + 255) & ~(size_t)255);
+    im_status rs = exclusive_scan_i32_to_i64(sizes, toff, n, nullptr, scan_tmp, scan_tmp_bytes(n),
+                                             st);
+    if (rs != IM_OK) return rs;
+    int64_t tree_total = 0;
+    IM_CUDA(cudaMemcpyAsync(&tree_total, toff + n, 8, cudaMemcpyDeviceToHost, st));
+    IM_CUDA(cudaStreamSynchronize(st));
+    IM_CUDA(cudaMalloc(&g->lt_leaf, (size_t)std::max<int64_t>(m, 1) * 8));
+    IM_CUDA(cudaMalloc(&g->lt_tree, (size_t)std::max<int64_t>(tree_total, 1) * 8));
+    IM_CUDA(cudaMalloc(&g->lt_vrec, (size_t)n * sizeof(uint4)));
+    {
+        KernelTimer kt(st, "lt_index");
+        k_lt_index<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, toff, g->lt_leaf,
+                                                  g->lt_tree, g->lt_vrec, n, d_invalid);
+    }
+    IM_CUDA(cudaGetLastError());
     int invalid = 0;
     IM_CUDA(cudaMemcpyAsync(&invalid, d_invalid, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IM_CUDA(cudaFreeAsync(sizes, st));
+    IM_CUDA(cudaFreeAsync(toff, st));
+    IM_CUDA(cudaFreeAsync(d_invalid, st));
     IM_CUDA(cudaStreamSynchronize(st));
-    cudaFree(d_invalid);
     g->lt_valid = invalid ? 0 : 1;
     return IM_OK;
 }
@@ -587,7 +659,7 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
                         uint64_t count, im_pool *pool, cudaStream_t st) {
     im_graph *g = const_cast<im_graph *>(gc);
     if (model == IM_LT) {
-        im_status s = build_lt_cdf(g, st);
+        im_status s = build_lt_index(g, st);
         if (s != IM_OK) return s;
         if (!g->lt_valid) {
             set_error("LT sampling needs every vertex's in-weights to sum to at most 2^32");
@@ -653,7 +725,9 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     a.in_off = g->in_off;
     a.in_src = g->in_src;
     a.w = g->w;
-    a.cdf = g->lt_cdf;
+    a.lt_vrec = g->lt_vrec;
+    a.lt_leaf = g->lt_leaf;
+    a.lt_tree = g->lt_tree;
     a.seed = seed;
     a.first = (uint32_t)first;
     a.count = cnt;
@@ -674,7 +748,6 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     a.ovf_count = ctr + 3;
     a.status = (int *)(ctr + 4);
     pool->index_valid = false;
-    pool->pkeys_valid = false;
 
     auto launch = [&](int nblocks) {
         KernelTimer kt(st, model == IM_LT ? "sample_lt" : "sample_ic");

@@ -82,6 +82,7 @@ def lib():
             "im_randgreedi_details": ([vp] + [vp] * 12 + [vp], ctypes.c_int),
             "im_partition": ([i64, i32, u64, vp, vp], ctypes.c_int),
             "im_pool_sample_bytes": ([vp, vp], ctypes.c_int),
+            "im_randgreedi_stats": ([vp, vp, vp], ctypes.c_int),
             "im_profile_enable": ([i32], ctypes.c_int),
             "im_profile_reset": ([], ctypes.c_int),
             "im_profile_read": ([i32, vp, vp, vp, vp], ctypes.c_int),
@@ -224,6 +225,12 @@ def im_randgreedi_details(p, local_seeds=None, local_gains=None, local_n=None, l
 
 def im_partition(n: int, P: int, partition_seed: int, part, stream=None):
     _check(lib().im_partition(n, P, partition_seed, _ptr(part), _stream(stream)), "im_partition")
+
+
+def im_randgreedi_stats(p, P: int, B: int, stream=None) -> np.ndarray:
+    out = np.zeros((P + B) * 6, np.int64)
+    _check(lib().im_randgreedi_stats(p, out.ctypes.data, _stream(stream)), "im_randgreedi_stats")
+    return out.reshape(P + B, 6)
 
 
 def im_pool_sample_bytes(p) -> int:
