@@ -5,8 +5,10 @@ One step = the whole hot path over one batch of synthetic input:
   RRR sampling of theta sets (im_sample_rrr: walk kernel, scan, per-set sort)
   -> covering-subset index (histogram, scan, scatter)
   -> plain greedy max-k-cover                        (im_max_k_cover, greedy)
-  -> RandGreedi: 148 vertex parts, local greedy + streaming threshold buckets,
-     truncated to the first ceil(k/4) local seeds    (im_max_k_cover, RandGreedi)
+  -> RandGreedi: 148 vertex parts, lazy local greedy, then the streaming
+     threshold buckets over the first ceil(k/4) local seeds of every part, each
+     bucket's bitmap in the shared memory of a thread-block cluster
+                                                     (im_max_k_cover, RandGreedi)
 Workload: R-MAT scale 20 (1,048,576 vertices, 16,777,216 edges, a/b/c/d =
 0.57/0.19/0.19/0.05, seed 42), LT weights 1/in-degree quantised to uint32,
 theta = 4,194,304, k = 100, delta = 0.077.
@@ -66,7 +68,7 @@ def parse():
     ap.add_argument("--theta", type=int, default=THETA, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--rg-fused", type=int, default=1,
+    ap.add_argument("--rg-fused", type=int, default=0,
                     help="RandGreedi as one cooperative launch (1) or two launches (0)")
     return ap.parse_args()
 

@@ -67,8 +67,11 @@ typedef enum { IM_GREEDY_PLAIN = 0, IM_RANDGREEDI = 1 } im_cover_algo;
  *   partition_seed  Philox key of the vertex partition (Alg. 3).
  *   fused           RandGreedi only: 1 runs local greedy and aggregation in
  *                   one cooperative launch with the aggregator consuming seeds
- *                   as they are produced (streaming overlap); 0 runs them as
- *                   two launches.  Results are identical. */
+ *                   as they are produced (streaming overlap, bucket bitmaps in
+ *                   global memory); 0 runs them as two launches, the second
+ *                   keeping each bucket's bitmap in the shared memory of a
+ *                   thread-block cluster (see IM_TUNE_RG_CLUSTER).  Results
+ *                   are identical. */
 typedef struct {
     int32_t algo;
     int32_t partitions;
@@ -175,6 +178,18 @@ im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out
  *       weights) + 4 when an edge is picked (its source) + 4 (member write),
  *       per set 8 (offset). */
 im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
+
+/* ---- tuning knobs (process-wide; results never depend on them) ---------------
+ *   IM_TUNE_LT_GROUP    lanes that run one LT walk: 8, 16 or 32 (default 8; a warp
+ *                       then runs 32 / value walks at once).
+ *   IM_TUNE_RG_CLUSTER  RandGreedi two-launch mode, bucket stage: 0 (default)
+ *                       picks the smallest cluster of 1, 2, 4 or 8 blocks whose
+ *                       shared memory holds a bucket's theta-bit bitmap; 1..8
+ *                       asks for at least that many; -1 keeps the bitmaps in
+ *                       global memory (one block per bucket). */
+typedef enum { IM_TUNE_LT_GROUP = 0, IM_TUNE_RG_CLUSTER = 1 } im_tune_knob;
+im_status im_tune_set(int32_t knob, int64_t value);
+im_status im_tune_get(int32_t knob, int64_t *value);
 
 /* ---- per-kernel device timing (tracing) -------------------------------------
  * While enabled, every kernel the library launches is bracketed by a pair of

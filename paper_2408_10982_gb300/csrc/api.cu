@@ -95,6 +95,16 @@ KernelTimer::~KernelTimer() {
     if (g_prof_pending.size() > 4096) prof_drain_locked();
 }
 
+namespace {
+std::mutex g_tune_mu;
+int64_t g_tune[2] = {8, 0};   // IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER
+}  // namespace
+
+int64_t tune_value(int32_t knob) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (knob >= 0 && knob < 2) ? g_tune[knob] : 0;
+}
+
 int num_sms() {
     static int cached[64] = {0};
     int dev = 0;
@@ -532,6 +542,27 @@ im_status im_randgreedi_stats(const im_pool *p, int64_t *stats, void *stream) {
 im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes) {
     if (!p || !bytes) return IM_ERR_INVALID_ARG;
     *bytes = p->sample_bytes;
+    return IM_OK;
+}
+
+im_status im_tune_set(int32_t knob, int64_t value) {
+    const bool ok = (knob == IM_TUNE_LT_GROUP && (value == 8 || value == 16 || value == 32)) ||
+                    (knob == IM_TUNE_RG_CLUSTER &&
+                     (value == -1 || value == 0 || value == 1 || value == 2 || value == 4 ||
+                      value == 8));
+    if (ok) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[knob] = value;
+        return IM_OK;
+    }
+    set_error("im_tune_set: unknown knob or value out of range");
+    return IM_ERR_INVALID_ARG;
+}
+
+im_status im_tune_get(int32_t knob, int64_t *value) {
+    if (!value || (knob != IM_TUNE_LT_GROUP && knob != IM_TUNE_RG_CLUSTER))
+        return IM_ERR_INVALID_ARG;
+    *value = tune_value(knob);
     return IM_OK;
 }
 

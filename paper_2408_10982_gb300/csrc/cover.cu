@@ -19,11 +19,15 @@
 // so the buckets see the same stream order in every run.  In the fused mode
 // producers and consumers are one cooperative launch (co-resident), so the
 // aggregation overlaps the local greedy as in the paper's streaming design.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace im {
 
@@ -34,6 +38,7 @@ constexpr int kRGThreads = 512;
 constexpr int kBatch = 256;                  // stream slots a consumer reads at once
 constexpr int kUnroll = 8;                   // independent loads in flight per lane in scans
 constexpr int kSpec = 32;                    // largest speculative group of stream elements
+constexpr size_t kClusterSmemCap = 200 * 1024;  // bucket bitmap slice per block
 
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v,
                                                             unsigned long long *sh) {
@@ -66,6 +71,38 @@ __device__ __forceinline__ long long block_sum_i64(long long v, long long *sh) {
     const long long r = sh[32];
     __syncthreads();
     return r;
+}
+
+// Calls f(id) for every entry of ids[off, off + len) with 16-byte vector
+// loads for the aligned body (each thread keeps U of them in flight) and
+// scalar loads for the unaligned head and tail; f gets -1 for padding.
+// Every thread of the calling group (tid < nth, nth >= 64) must call it.
+template <int U, typename F>
+__device__ __forceinline__ void scan_ids(const int32_t *__restrict__ ids, int64_t off, int64_t len,
+                                         int tid, int nth, F &&f) {
+    const int64_t end = off + len;
+    int64_t a4 = (off + 3) & ~(int64_t)3;
+    if (a4 > end) a4 = end;
+    const int64_t b4 = a4 + ((end - a4) & ~(int64_t)3);
+    if (tid < a4 - off) f(__ldg(ids + off + tid));
+    else if (tid >= 32 && tid - 32 < end - b4) f(__ldg(ids + b4 + (tid - 32)));
+    const int4 *v = reinterpret_cast<const int4 *>(ids + a4);
+    const int64_t n4 = (b4 - a4) >> 2;
+    for (int64_t i = tid; i < n4; i += (int64_t)nth * U) {
+        int4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t k = i + (int64_t)u * nth;
+            w[u] = k < n4 ? __ldg(v + k) : make_int4(-1, -1, -1, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            f(w[u].x);
+            f(w[u].y);
+            f(w[u].z);
+            f(w[u].w);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -229,17 +266,9 @@ __device__ void produce(const RGArgs &a, int p, int32_t *key, unsigned long long
         if (stamp[l] != j) {
             // stale: recompute |S(v) \ covered| and retry the round
             long long miss = 0;
-            for (int64_t t0 = sb + threadIdx.x; t0 < se; t0 += (int64_t)blockDim.x * kUnroll) {
-                int32_t ids[kUnroll];
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int64_t t = t0 + (int64_t)u * blockDim.x;
-                    ids[u] = t < se ? __ldg(a.set_ids + t) : -1;
-                }
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u)
-                    if (ids[u] >= 0) miss += !((__ldcg(cov + (ids[u] >> 5)) >> (ids[u] & 31)) & 1u);
-            }
+            scan_ids<4>(a.set_ids, sb, se - sb, threadIdx.x, blockDim.x, [&](int32_t i) {
+                if (i >= 0) miss += !((__ldcg(cov + (i >> 5)) >> (i & 31)) & 1u);
+            });
             const long long g = block_sum_i64(miss, shs);
             if (threadIdx.x == 0) {
                 key[l] = (int32_t)g;
@@ -262,10 +291,9 @@ __device__ void produce(const RGArgs &a, int p, int32_t *key, unsigned long long
         }
         total += gain;
         cover_entries += se - sb;
-        for (int64_t t = sb + threadIdx.x; t < se; t += blockDim.x) {
-            const int32_t i = a.set_ids[t];
-            atomicOr(&cov[i >> 5], 1u << (i & 31));
-        }
+        scan_ids<4>(a.set_ids, sb, se - sb, threadIdx.x, blockDim.x, [&](int32_t i) {
+            if (i >= 0) atomicOr(&cov[i >> 5], 1u << (i & 31));
+        });
         __syncthreads();
         ++j;
     }
@@ -455,6 +483,157 @@ __global__ void __launch_bounds__(kRGThreads) k_randgreedi(RGArgs a) {
     }
 }
 
+// Streaming buckets with the bucket bitmap in shared memory (Alg. 5, run after
+// the local greedy has finished).  A cluster of CS blocks serves one bucket
+// at a time (buckets are taken from a global counter): block r keeps the bits
+// of set ids [r * R, (r + 1) * R) in its shared memory, scans every entry of
+// S(x) and tests only the ids in its own range.  The per-candidate counts of
+// the CS blocks are added over distributed shared memory after a cluster
+// barrier, and every block takes the same accept decision.  Candidates go in
+// the same speculative groups as in consume(); partial-count arrays alternate
+// between two buffers so one barrier per group suffices.
+__global__ void __launch_bounds__(kRGThreads) k_rg_stream_cluster(RGArgs a, int64_t R,
+                                                                  unsigned *bucket_counter) {
+    extern __shared__ uint32_t bits[];               // R bits, then 2 x kSpec partial counts
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned CS = cluster.num_blocks();
+    const unsigned rank = cluster.block_rank();
+    const int64_t words = R / 32;
+    unsigned *part = bits + words;                   // [2][kSpec]
+    __shared__ int32_t w_x[kBatch];                  // stream window: element, offset, length
+    __shared__ int64_t w_off[kBatch], w_len[kBatch];
+    __shared__ int s_cand[kSpec];
+    __shared__ unsigned long long s_tot[kSpec];
+    __shared__ int s_n, s_bucket, s_end, s_acc;
+    const int64_t lo = (int64_t)rank * R;
+    const int lane = threadIdx.x & 31;
+    const int64_t E = (int64_t)a.trunc * a.P;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) s_bucket = (int)atomicAdd(bucket_counter, 1u);
+        cluster.sync();
+        if (threadIdx.x == 0) s_bucket = *cluster.map_shared_rank(&s_bucket, 0);
+        cluster.sync();
+        const int b = s_bucket;
+        if (b >= a.B) break;
+        for (int64_t x = threadIdx.x; x < words; x += blockDim.x) bits[x] = 0u;
+        const int64_t T = a.thr[b];
+        const uint64_t t_begin = global_ns();
+        long long n_eval = 0, scanned = 0;
+        int32_t bn = 0;
+        int64_t bcov = 0;
+        int W = 1, phase = 0;
+        cluster.sync();
+        for (int64_t base = 0; base < E && bn < a.k; base += kBatch) {
+            // the producers have finished: every slot is final (1 seed, 2 none)
+            const int cntb = (int)min((int64_t)kBatch, E - base);
+            if (threadIdx.x < cntb) {
+                const int64_t slot = base + threadIdx.x;
+                int32_t x = -1;
+                int64_t off = 0, len = 0;
+                if (ld_acquire_u32(a.flags + slot) == 1u) {
+                    x = __ldcg(a.elems + slot);
+                    off = a.vtx_off[x];
+                    len = a.vtx_off[x + 1] - off;
+                }
+                w_x[threadIdx.x] = x;
+                w_off[threadIdx.x] = off;
+                w_len[threadIdx.x] = len;
+            }
+            __syncthreads();
+            int qq = 0;
+            while (qq < cntb && bn < a.k) {
+                if (threadIdx.x == 0) {
+                    // next W candidates; |S(x)| < threshold rejects x without a scan
+                    int n = 0, r = qq;
+                    while (r < cntb && n < W) {
+                        if (w_x[r] >= 0 && w_len[r] >= T) s_cand[n++] = r;
+                        ++r;
+                    }
+                    s_n = n;
+                    s_end = r;
+                }
+                unsigned *mine = part + phase * kSpec;
+                if (threadIdx.x < kSpec) mine[threadIdx.x] = 0u;
+                __syncthreads();
+                const int n = s_n;
+                if (n == 0) {
+                    qq = s_end;
+                    __syncthreads();
+                    continue;
+                }
+                for (int c = 0; c < n; ++c) {
+                    const int r = s_cand[c];
+                    unsigned m = 0;
+                    scan_ids<4>(a.set_ids, w_off[r], w_len[r], threadIdx.x, blockDim.x,
+                                [&](int32_t id) {
+                                    const int64_t rel = (int64_t)id - lo;
+                                    if (id >= 0 && rel >= 0 && rel < R)
+                                        m += !((bits[rel >> 5] >> (rel & 31)) & 1u);
+                                });
+                    m = warp_sum<unsigned>(m);
+                    if (lane == 0 && m) atomicAdd(&mine[c], m);
+                }
+                cluster.sync();
+                // candidate c's total over the cluster, summed by thread c
+                if (threadIdx.x < n) {
+                    unsigned long long tot = 0;
+                    for (unsigned r2 = 0; r2 < CS; ++r2)
+                        tot += cluster.map_shared_rank(mine, r2)[threadIdx.x];
+                    s_tot[threadIdx.x] = tot;
+                }
+                __syncthreads();
+                if (threadIdx.x < 32) {
+                    const bool ok = lane < n && (int64_t)s_tot[lane] >= T;
+                    const unsigned bal = __ballot_sync(kFull, ok);
+                    if (lane == 0) s_acc = bal ? __ffs(bal) - 1 : -1;
+                }
+                __syncthreads();
+                const int acc = s_acc;
+                n_eval += acc < 0 ? n : acc + 1;
+                for (int c = 0; c < n; ++c) scanned += w_len[s_cand[c]];
+                if (acc < 0) {
+                    qq = s_end;
+                    W = min(kSpec, 2 * W);
+                } else {
+                    const int r = s_cand[acc];
+                    scan_ids<4>(a.set_ids, w_off[r], w_len[r], threadIdx.x, blockDim.x,
+                                [&](int32_t id) {
+                                    const int64_t rel = (int64_t)id - lo;
+                                    if (id >= 0 && rel >= 0 && rel < R)
+                                        atomicOr(&bits[rel >> 5], 1u << (rel & 31));
+                                });
+                    const int64_t gain = (int64_t)s_tot[acc];
+                    if (rank == 0 && threadIdx.x == 0) {
+                        a.bucket_seeds[(int64_t)b * a.k + bn] = w_x[r];
+                        a.bucket_gains[(int64_t)b * a.k + bn] = gain;
+                    }
+                    ++bn;
+                    bcov += gain;
+                    qq = r + 1;
+                    W = max(1, W / 2);
+                }
+                phase ^= 1;
+                __syncthreads();
+            }
+            __syncthreads();
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            a.bucket_n[b] = bn;
+            a.bucket_cov[b] = bcov;
+            if (a.stats) {
+                long long *st = a.stats + 6 * ((int64_t)a.P + b);
+                st[0] = (long long)t_begin;
+                st[1] = (long long)global_ns();
+                st[2] = n_eval;
+                st[3] = bn;
+                st[4] = scanned;
+                st[5] = 0;
+            }
+        }
+        cluster.sync();
+    }
+}
+
 // Alg. 4's final compare: best bucket (ties: smallest b) against the best
 // local solution (ties: smallest p); the bucket wins ties.
 __global__ void k_rg_final(RGArgs a, int32_t *seeds, int64_t *gains, int32_t *nseeds,
@@ -619,7 +798,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     const size_t o_bcov = take((size_t)B * words * 4);
     const size_t o_flags = take((size_t)trunc * P * 4);
     const size_t o_elems = take((size_t)trunc * P * 4);
-    const size_t o_l = take(8);
+    const size_t o_l = take(64);
     void *base = nullptr;
     s = pool_scratch(p, off, &base);
     if (s != IM_OK) return s;
@@ -699,13 +878,46 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
             k_randgreedi<<<a.nprod, kRGThreads, prod_smem, st>>>(a);
         }
         IM_CUDA(cudaGetLastError());
-        a.ncons = std::min<int32_t>(B, resident);
-        a.first_role = 1;
-        {
-            KernelTimer kt(st, "randgreedi_stream");
-            k_randgreedi<<<a.ncons, kRGThreads, prod_smem, st>>>(a);
+        // buckets: shared-memory bitmaps split over a cluster when theta fits
+        const int64_t want = tune_value(IM_TUNE_RG_CLUSTER);   // 0 auto, -1 off, 1..8
+        int CS = want > 0 ? (int)want : 1;
+        int64_t R = 0;
+        size_t csmem = 0;
+        for (; CS <= 8; CS *= 2) {
+            R = (theta + (int64_t)CS * 32 - 1) / ((int64_t)CS * 32) * 32;
+            csmem = (size_t)(R / 8) + 2 * kSpec * sizeof(unsigned);
+            if (csmem <= kClusterSmemCap) break;
         }
-        IM_CUDA(cudaGetLastError());
+        if (want < 0) CS = 16;   // global-memory bitmaps requested
+        if (CS <= 8) {
+            unsigned *counter = (unsigned *)(Bs + o_l) + 2;
+            IM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+            IM_CUDA(cudaFuncSetAttribute(k_rg_stream_cluster,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+            const int nclusters = std::max(1, std::min<int>(B, num_sms() / CS));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(nclusters * CS);
+            cfg.blockDim = dim3(kRGThreads);
+            cfg.dynamicSmemBytes = csmem;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = CS;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            KernelTimer kt(st, "randgreedi_stream");
+            IM_CUDA(cudaLaunchKernelEx(&cfg, k_rg_stream_cluster, a, R, counter));
+        } else {
+            a.ncons = std::min<int32_t>(B, resident);
+            a.first_role = 1;
+            {
+                KernelTimer kt(st, "randgreedi_stream");
+                k_randgreedi<<<a.ncons, kRGThreads, prod_smem, st>>>(a);
+            }
+            IM_CUDA(cudaGetLastError());
+        }
     }
     int32_t *d_chosen = (int32_t *)(Bs + o_l);   // l is no longer needed
     {

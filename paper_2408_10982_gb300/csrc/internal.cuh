@@ -239,6 +239,9 @@ class KernelTimer {
     bool on_ = false;
 };
 
+// process-wide tuning knobs (im_tune_set); results never depend on them
+int64_t tune_value(int32_t knob);
+
 // scratch arena of a pool: returns a pointer to at least `bytes` (256-aligned)
 im_status pool_scratch(im_pool *p, size_t bytes, void **out);
 

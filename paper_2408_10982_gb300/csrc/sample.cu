@@ -22,9 +22,10 @@ namespace {
 constexpr int kSampleThreads = 256;          // 8 warps per block
 constexpr int kWarps = kSampleThreads / 32;
 constexpr int64_t kSmemVisBits = 1 << 16;    // visited bitmap in smem when n <= this
-constexpr int kPathSmem = 256;               // LT path entries mirrored in smem
+constexpr int kPathSmem = 256;               // LT path entries mirrored in smem (warp walks)
+constexpr int kPathSmemGroup = 64;           // ... per walk when a warp runs several walks
 constexpr int64_t kQueueCapIC = 1 << 14;     // per-warp queue entries (first pass)
-constexpr int64_t kQueueCapLT = 1 << 12;
+constexpr int64_t kQueueCapLT = 1 << 11;
 constexpr int kWarpSortBytes = 4096;         // per-warp smem sort buffer
 constexpr int kBlockSortCap = 16384;         // ... by one block in shared memory (int32)
 
@@ -235,110 +236,176 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
 // ceil(log32 d) + 1 coalesced loads instead of scattered probes, and the leaf
 // that matches also carries the source id.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int lt_levels(int64_t d) {
-    int L = 0;
-    while (d > 32) {
-        d = (d + 31) >> 5;
-        ++L;
-    }
-    return L;
+// Group-wide helpers: a group is G consecutive lanes of a warp running one walk.
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    return G == 32 ? kFull : (((1u << G) - 1u) << ((lane / G) * G));
 }
 
-__global__ void __launch_bounds__(kSampleThreads, 8) k_sample_lt(SampleArgs a) {
-    __shared__ int32_t spath[kWarps][kPathSmem];
+// One walk per group of G lanes; a warp runs 32 / G walks in lockstep.  The
+// loop is warp-uniform: every iteration each group advances its own walk by
+// one step (groups without a walk idle through predication, so the warp never
+// splits and the Philox draw, the search and the revisit test of all its
+// walks share one instruction stream); a group whose walk ended emits it and
+// takes the next sample at the top of the next iteration.  Every level of the
+// search tree is a window of up to 32 values; lane l of a group holds values
+// [l * 32/G, (l + 1) * 32/G) of it.
+template <int G>
+__global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 6) k_sample_lt(SampleArgs a) {
+    constexpr int NG = 32 / G;                       // walks per warp
+    constexpr int NV = 32 / G;                       // window values per lane
+    constexpr int PS = G == 32 ? kPathSmem : kPathSmemGroup;
+    constexpr unsigned GBITS = G == 32 ? kFull : ((1u << G) - 1u);
+    __shared__ int32_t spath[kWarps * NG][PS];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * kWarps + wib;
-    int32_t *q = a.queues + (size_t)gw * (size_t)a.qcap;
-    int32_t *sp = spath[wib];
+    const int grp = lane / G, gl = lane % G, gbase = grp * G;
+    const unsigned gmask = group_mask<G>(lane);
+    const int64_t slot = ((int64_t)blockIdx.x * kWarps + wib) * NG + grp;
+    int32_t *q = a.queues + (size_t)slot * (size_t)a.qcap;
+    int32_t *sp = spath[wib * NG + grp];
     const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
     unsigned long long exam = 0, abytes = 0;
+    bool active = false, exhausted = false;
+    int64_t j = 0;
+    uint32_t s = 0, cur = 0;
+    int32_t len = 0;
+    unsigned long long sexam = 0;
+    uint32_t sbytes = 0;   // flushed into abytes before it can wrap
     for (;;) {
-        const int64_t j = next_item(a, lane);
-        if (j < 0) break;
-        const uint32_t s = a.first + (uint32_t)j;
-        uint32_t cur = rrr_root(a.seed, s, a.n);
-        if (lane == 0) {
-            q[0] = (int32_t)cur;
-            sp[0] = (int32_t)cur;
+        if (!active && !exhausted) {                 // group-uniform
+            unsigned long long jw = 0;
+            if (gl == 0) jw = atomicAdd(a.work, 1ull);
+            jw = __shfl_sync(gmask, jw, 0, G);
+            if (jw < (unsigned long long)a.count) {
+                j = a.list ? a.list[jw] : (int64_t)jw;
+                s = a.first + (uint32_t)j;
+                cur = rrr_root(a.seed, s, a.n);
+                if (gl == 0) {
+                    q[0] = (int32_t)cur;
+                    sp[0] = (int32_t)cur;
+                }
+                len = 1;
+                sexam = 0;
+                sbytes = 8;
+                active = true;
+            } else {
+                exhausted = true;
+            }
         }
         __syncwarp();
-        int32_t len = 1;
-        bool overflow = false;
-        unsigned long long sexam = 0;
-        uint32_t sbytes = 8;   // flushed into abytes before it can wrap
-        for (;;) {
-            const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
-            const unsigned long long xs = (unsigned long long)x;
-            const uint4 vr = __ldg(a.lt_vrec + cur);
-            const int64_t eb = vr.x, d = vr.y;
-            int64_t pick = -1;
-            unsigned long long leaf = 0;
-            if (d > 0) {
-                const int L = lt_levels(d);
-                const unsigned long long *lvl = a.lt_tree + vr.z;   // levels stored top-down
-                int64_t blk = 0;
-                bool none = false;
-                for (int l = L; l >= 1; --l) {
-                    const int64_t sz = (d + (1ll << (5 * l)) - 1) >> (5 * l);
-                    const int64_t idx = blk * 32 + lane;
-                    const bool pr = idx < sz && xs < __ldg(lvl + idx);
-                    const unsigned bal = __ballot_sync(kFull, pr);
-                    if (!bal) {
-                        none = true;
-                        break;
-                    }
-                    blk = blk * 32 + (__ffs(bal) - 1);
+        if (!__any_sync(kFull, active)) break;
+
+        // ---- one step of every active walk ----
+        const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
+        const unsigned long long xs = (unsigned long long)x;
+        const uint4 vr = active ? __ldg(a.lt_vrec + cur) : make_uint4(0u, 0u, 0u, 0u);
+        const int32_t d = (int32_t)vr.y;
+        bool live = active && d > 0;                 // group-uniform
+        const int lmax = (int)__reduce_max_sync(kFull, live ? vr.w : 0u);
+        const unsigned long long *lvl = a.lt_tree + vr.z;   // levels stored top-down
+        int32_t blk = 0;
+        for (int l = lmax; l >= 1; --l) {
+            const bool here = live && l <= (int)vr.w;
+            const int32_t sz = here ? (int32_t)(((int64_t)d + (1ll << (5 * l)) - 1) >> (5 * l)) : 0;
+            int lf = NV;
+#pragma unroll
+            for (int v = NV - 1; v >= 0; --v) {
+                const int32_t idx = blk * 32 + gl * NV + v;
+                if (idx < sz && xs < __ldg(lvl + idx)) lf = v;
+            }
+            const unsigned bal = (__ballot_sync(kFull, lf < NV) >> gbase) & GBITS;
+            const int f = bal ? __ffs(bal) - 1 : 0;
+            const int lfv = __shfl_sync(kFull, lf, gbase + f);
+            if (here) {
+                if (!bal) live = false;
+                else {
+                    blk = blk * 32 + f * NV + lfv;
                     lvl += sz;
                 }
-                if (!none) {
-                    const int64_t idx = blk * 32 + lane;
-                    unsigned long long r = 0;
-                    if (idx < d) r = __ldg(a.lt_leaf + eb + idx);
-                    const bool pr = idx < d && xs < (r >> 31);
-                    const unsigned bal = __ballot_sync(kFull, pr);
-                    if (bal) {
-                        const int f = __ffs(bal) - 1;
-                        pick = blk * 32 + f;
-                        leaf = __shfl_sync(kFull, r, f);
+            }
+        }
+        int32_t pick = -1;
+        unsigned long long leaf = 0;
+        {
+            int lf = NV;
+            unsigned long long hit = 0;
+#pragma unroll
+            for (int v = NV - 1; v >= 0; --v) {
+                const int32_t idx = blk * 32 + gl * NV + v;
+                if (live && idx < d) {
+                    const unsigned long long r = __ldg(a.lt_leaf + vr.x + idx);
+                    if (xs < (r >> 31)) {
+                        lf = v;
+                        hit = r;
                     }
                 }
             }
-            if (lane == 0) {
-                sexam += (unsigned long long)(pick >= 0 ? pick + 1 : d);
-                // offsets, binary search of d cumulative weights, source, member write
-                sbytes += 16u + (d > 0 ? 8u * (uint32_t)(32 - __clz((uint32_t)d)) : 0u) +
-                          (pick >= 0 ? 4u : 0u) + 4u;
-                if (sbytes > (1u << 30)) {   // only long walks of the second pass get here
-                    abytes += sbytes;
-                    sbytes = 0;
-                }
+            const unsigned bal = (__ballot_sync(kFull, lf < NV) >> gbase) & GBITS;
+            const int f = bal ? __ffs(bal) - 1 : 0;
+            const int lfv = __shfl_sync(kFull, lf, gbase + f);
+            const unsigned long long hv = __shfl_sync(kFull, hit, gbase + f);
+            if (live && bal) {
+                pick = blk * 32 + f * NV + lfv;
+                leaf = hv;
             }
-            if (pick < 0) break;
-            const int32_t u = (int32_t)(leaf & 0x7fffffffull);
-            bool seen = false;
-            const int32_t ls = len < kPathSmem ? len : kPathSmem;
-            for (int32_t i = lane; i < ls; i += 32) seen |= sp[i] == u;
-            for (int32_t i = kPathSmem + lane; i < len; i += 32) seen |= q[i] == u;
-            if (__any_sync(kFull, seen)) break;
-            if (len >= a.qcap) {
-                overflow = true;
-                break;
+        }
+        if (active && gl == 0) {
+            sexam += (unsigned long long)(pick >= 0 ? pick + 1 : d);
+            // offsets, binary search of d cumulative weights, source, member write
+            sbytes += 16u + (d > 0 ? 8u * (uint32_t)(32 - __clz((uint32_t)d)) : 0u) +
+                      (pick >= 0 ? 4u : 0u) + 4u;
+            if (sbytes > (1u << 30)) {   // only long walks of the second pass get here
+                abytes += sbytes;
+                sbytes = 0;
             }
-            if (lane == 0) {
+        }
+        // revisit test of the picked source against the walk so far
+        const bool picked = active && pick >= 0;
+        const int32_t u = (int32_t)(leaf & 0x7fffffffull);
+        const int lenmax = (int)__reduce_max_sync(kFull, picked ? (unsigned)len : 0u);
+        bool seen = false;
+        for (int32_t i = gl; i < lenmax; i += G)
+            if (picked && i < len) seen |= (i < PS ? sp[i] : q[i]) == u;
+        const bool seen_g = ((__ballot_sync(kFull, seen) >> gbase) & GBITS) != 0;
+        const bool grow = picked && !seen_g && len < a.qcap;
+        const bool ovf = picked && !seen_g && len >= a.qcap;
+        if (grow) {
+            if (gl == 0) {
                 q[len] = u;
-                if (len < kPathSmem) sp[len] = u;
+                if (len < PS) sp[len] = u;
             }
-            __syncwarp();
             ++len;
             cur = (uint32_t)u;
         }
         __syncwarp();
-        if (overflow) {
-            mark_overflow(a, j, lane);
-        } else {
-            emit_set(a, j, q, len, lane);
-            exam += sexam;
-            if (lane == 0) abytes += sbytes;
+        if (active && !grow) {                       // the walk ended: emit it
+            if (ovf) {
+                if (gl == 0) {
+                    a.sizes[j] = -1;
+                    a.stage_off[j] = 0;
+                    a.ovf_list[atomicAdd(a.ovf_count, 1ull)] = j;
+                }
+            } else {
+                unsigned long long pos = 0;
+                if (gl == 0) pos = atomicAdd(a.stage_cursor, (unsigned long long)len);
+                pos = __shfl_sync(gmask, pos, 0, G);
+                if ((int64_t)pos + len > a.stage_cap) {
+                    if (gl == 0) {
+                        raise_status(a.status, kDevStageOverflow);
+                        a.sizes[j] = 0;
+                        a.stage_off[j] = 0;
+                    }
+                } else {
+                    for (int32_t i = gl; i < len; i += G) a.stage[pos + i] = i < PS ? sp[i] : q[i];
+                    if (gl == 0) {
+                        a.stage_off[j] = (int64_t)pos;
+                        a.sizes[j] = len;
+                    }
+                }
+                exam += sexam;
+                if (gl == 0) abytes += sbytes;
+            }
+            active = false;
         }
         __syncwarp();
     }
@@ -348,7 +415,8 @@ __global__ void __launch_bounds__(kSampleThreads, 8) k_sample_lt(SampleArgs a) {
     if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
 }
 
-// LT search index.  For vertex v with in-edges [eb, eb + d):
+// LT search index.  vrec[v] = {eb, d, tree offset, number of upper levels L}.
+// For vertex v with in-edges [eb, eb + d):
 //   leaf[e] = (sum of w over v's in-edges up to and including e) << 31 | src(e)
 // (the running sum is at most 2^32 for valid LT weights -- 33 bits -- and
 // source ids stay below 2^31, so the pair packs into 64 bits), and for
@@ -387,11 +455,12 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
             carry += __shfl_sync(kFull, incl, 31);
         }
         if (lane == 0 && carry > (1ull << 32)) atomicExch(invalid, 1);
-        if (lane == 0) vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], 0u);
-        __syncwarp();
-        // upper levels, top-down
         int L = 0;
         for (int64_t t = d; t > 32; t = (t + 31) >> 5) ++L;
+        if (lane == 0)
+            vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], (uint32_t)L);
+        __syncwarp();
+        // upper levels, top-down
         unsigned long long *lvl = tree + tree_off[v];
         for (int l = L; l >= 1; --l) {
             const int64_t sz = (d + (1ll << (5 * l)) - 1) >> (5 * l);
@@ -677,9 +746,13 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     const int64_t vis_words = (n + 31) / 32;
 
     // launch shape: persistent, occupancy-sized
-    const void *kern = model == IM_LT ? (const void *)k_sample_lt
-                       : smem_vis   ? (const void *)k_sample_ic<true>
-                                    : (const void *)k_sample_ic<false>;
+    const int G = model == IM_LT ? (int)tune_value(IM_TUNE_LT_GROUP) : 32;
+    const void *kern = model == IM_LT
+                           ? (G == 8    ? (const void *)k_sample_lt<8>
+                              : G == 16 ? (const void *)k_sample_lt<16>
+                                        : (const void *)k_sample_lt<32>)
+                       : smem_vis ? (const void *)k_sample_ic<true>
+                                  : (const void *)k_sample_ic<false>;
     const size_t dyn_smem = smem_vis ? (size_t)kWarps * vis_words * 4 : 0;
     if (smem_vis && dyn_smem > 48 * 1024)
         IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -692,6 +765,7 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
         blocks = (int)std::min<int64_t>(blocks, cap_blocks);
     }
     const int64_t warps = (int64_t)blocks * kWarps;
+    const int64_t slots = warps * (32 / G);           // one queue per walk in flight
     const int64_t qcap = std::min<int64_t>(n, model == IM_LT ? kQueueCapLT : kQueueCapIC);
 
     // scratch layout
@@ -707,7 +781,7 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     const size_t o_ovf = take((size_t)cnt * 8);
     const size_t o_scan = take(scan_tmp_bytes(cnt));
     const size_t o_sort = take((size_t)(2 + 2 * cnt) * 8);
-    const size_t o_q = take((size_t)warps * qcap * 4);
+    const size_t o_q = take((size_t)slots * qcap * 4);
     const size_t o_vis = take(model == IM_IC && !smem_vis ? (size_t)warps * vis_words * 4 : 0);
     void *base = nullptr;
     im_status rs = pool_scratch(pool, off, &base);
@@ -749,13 +823,19 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     a.status = (int *)(ctr + 4);
     pool->index_valid = false;
 
-    auto launch = [&](int nblocks) {
+    auto launch = [&](int nblocks, int group) {
         KernelTimer kt(st, model == IM_LT ? "sample_lt" : "sample_ic");
-        if (model == IM_LT) k_sample_lt<<<nblocks, kSampleThreads, 0, st>>>(a);
-        else if (smem_vis) k_sample_ic<true><<<nblocks, kSampleThreads, dyn_smem, st>>>(a);
-        else k_sample_ic<false><<<nblocks, kSampleThreads, 0, st>>>(a);
+        if (model == IM_LT) {
+            if (group == 8) k_sample_lt<8><<<nblocks, kSampleThreads, 0, st>>>(a);
+            else if (group == 16) k_sample_lt<16><<<nblocks, kSampleThreads, 0, st>>>(a);
+            else k_sample_lt<32><<<nblocks, kSampleThreads, 0, st>>>(a);
+        } else if (smem_vis) {
+            k_sample_ic<true><<<nblocks, kSampleThreads, dyn_smem, st>>>(a);
+        } else {
+            k_sample_ic<false><<<nblocks, kSampleThreads, 0, st>>>(a);
+        }
     };
-    launch(blocks);
+    launch(blocks, G);
     IM_CUDA(cudaGetLastError());
 
     unsigned long long hc[6];
@@ -785,7 +865,7 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
         a2.gvis = vis2;
         a2.ovf_list = a.ovf_list + cnt;   // never written: qcap = n cannot overflow
         a = a2;
-        launch(nb2);
+        launch(nb2, 32);   // one walk per warp: queues of n entries for the longest sets
         IM_CUDA(cudaGetLastError());
         IM_CUDA(cudaFreeAsync(q2, st));
         IM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));

@@ -83,6 +83,8 @@ def lib():
             "im_partition": ([i64, i32, u64, vp, vp], ctypes.c_int),
             "im_pool_sample_bytes": ([vp, vp], ctypes.c_int),
             "im_randgreedi_stats": ([vp, vp, vp], ctypes.c_int),
+            "im_tune_set": ([i32, i64], ctypes.c_int),
+            "im_tune_get": ([i32, vp], ctypes.c_int),
             "im_profile_enable": ([i32], ctypes.c_int),
             "im_profile_reset": ([], ctypes.c_int),
             "im_profile_read": ([i32, vp, vp, vp, vp], ctypes.c_int),
@@ -237,6 +239,20 @@ def im_pool_sample_bytes(p) -> int:
     b = ctypes.c_int64()
     _check(lib().im_pool_sample_bytes(p, ctypes.byref(b)), "im_pool_sample_bytes")
     return b.value
+
+
+IM_TUNE_LT_GROUP = 0
+IM_TUNE_RG_CLUSTER = 1
+
+
+def im_tune_set(knob: int, value: int):
+    _check(lib().im_tune_set(knob, value), "im_tune_set")
+
+
+def im_tune_get(knob: int) -> int:
+    v = ctypes.c_int64()
+    _check(lib().im_tune_get(knob, ctypes.byref(v)), "im_tune_get")
+    return v.value
 
 
 def im_profile_enable(on: bool = True):

@@ -235,3 +235,38 @@ def test_randgreedi_lt(im, fused, Pn, alpha):
 def test_randgreedi_ic_small(im, fused):
     g = inputs.graph_small_ic()
     _rg_compare(im, g, im.IM_IC, 16384, 16, 148, (1, 4), 0.077, fused)
+
+
+@pytest.mark.parametrize("group", [8, 16, 32])
+def test_lt_group_sizes_identical(im, group):
+    """Lanes per LT walk is a tuning knob: every setting gives the same pool."""
+    g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+    old = im.im_tune_get(im.IM_TUNE_LT_GROUP)
+    im.im_tune_set(im.IM_TUNE_LT_GROUP, group)
+    try:
+        G, P = gpu_pool(im, g, im.IM_LT, 7, [(0, 20000)])
+        assert_pool_equal(im, P, O.sample(O.LT, g, 7, 0, 20000))
+        gr = inputs.random_graph(60, 500, 9, "lt_random")
+        G2, P2 = gpu_pool(im, gr, im.IM_LT, 99, [(0, 999)])
+        assert_pool_equal(im, P2, O.sample(O.LT, gr, 99, 0, 999))
+    finally:
+        im.im_tune_set(im.IM_TUNE_LT_GROUP, old)
+
+
+@pytest.mark.parametrize("cluster", [-1, 1, 2, 4, 8])
+def test_randgreedi_bucket_stage_variants(im, cluster):
+    """Two-launch RandGreedi: every bucket-stage layout (global bitmaps, or a
+    shared-memory bitmap split over 1..8 blocks of a cluster) gives the oracle's result."""
+    old = im.im_tune_get(im.IM_TUNE_RG_CLUSTER)
+    im.im_tune_set(im.IM_TUNE_RG_CLUSTER, cluster)
+    try:
+        g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+        _rg_compare(im, g, im.IM_LT, 30000, 50, 148, (1, 4), 0.077, False)
+    finally:
+        im.im_tune_set(im.IM_TUNE_RG_CLUSTER, old)
+
+
+def test_randgreedi_large_theta_cluster(im):
+    """theta above one block's shared memory: the automatic cluster has >= 2 blocks."""
+    g = inputs.rmat_graph(1 << 12, 1 << 16, 5, "lt")
+    _rg_compare(im, g, im.IM_LT, 2_000_000, 40, 148, (1, 4), 0.077, False, seed=3)
