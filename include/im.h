@@ -212,6 +212,29 @@ im_status im_profile_read(int32_t max_entries, char *names, int64_t *launches, d
  *   elements accepted, entries scanned, ns spent waiting for the stream. */
 im_status im_randgreedi_stats(const im_pool *p, int64_t *stats, void *stream);
 
+/* Standard greedy max-k-cover (same result as im_max_k_cover with
+ * IM_GREEDY_PLAIN) for callers that cannot let the library allocate device
+ * memory -- a framework whose caching allocator owns the device memory, a
+ * serving loop that must not pay for cudaMalloc mid-request, a fixed memory
+ * budget.  The paper has no counterpart; this is a deployment variant.
+ * The caller passes the RRR sets (set_off int64[theta+1], members int32[T])
+ * and the covering subsets (vtx_off int64[n+1], set_ids int32[T]) -- e.g. as
+ * exported by im_pool_export / im_index_export -- and the outputs seeds
+ * int32[k], gains int64[k], num_seeds int32[1], coverage int64[1]; every
+ * array must be device memory.  The call allocates nothing: its scratch is a
+ * 64 MiB static device array inside the library, which every GPU that loads
+ * the library holds until the process exits.  It needs
+ * 4 n + theta / 8 + 33 KB bytes of it; larger instances get IM_ERR_CAPACITY.
+ * The first call on a device looks up that array's device address (keep it
+ * outside any stream capture).  All calls on a device share the one array,
+ * which keeps the previous call's contents: each call clears what must start
+ * at zero, but calls that overlap on the GPU (other streams or threads) race
+ * and must be serialised by the caller.  Synchronises the stream. */
+im_status im_max_k_cover_noalloc(const int64_t *set_off, const int32_t *members,
+                                 const int64_t *vtx_off, const int32_t *set_ids, int64_t n,
+                                 int64_t theta, int32_t k, int32_t *seeds, int64_t *gains,
+                                 int32_t *num_seeds, int64_t *coverage, void *stream);
+
 /* Vertex partition of Alg. 3: part[v] = (Philox(v,0,0,4).x * P) >> 32. */
 im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
                        void *stream);

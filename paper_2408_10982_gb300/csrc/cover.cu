@@ -725,6 +725,41 @@ im_status greedy_plain(im_pool *p, int32_t k, int32_t *d_seeds, int64_t *d_gains
     return IM_OK;
 }
 
+// Launches the standard greedy kernel on caller-provided scratch (used by the
+// allocation-free entry point in noalloc.cu; greedy_plain above is unchanged).
+im_status greedy_launch(int64_t n, int64_t theta, const int64_t *set_off, const int32_t *members,
+                        const int64_t *vtx_off, const int32_t *set_ids, int32_t k, int32_t *counts,
+                        uint32_t *covered, unsigned long long *block_best, int max_grid,
+                        void *barrier, int32_t *seeds, int64_t *gains, int32_t *nseeds,
+                        int64_t *coverage, int *status, cudaStream_t st) {
+    int per_sm = 0;
+    IM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy, kGreedyThreads, 0));
+    if (per_sm < 1) return IM_ERR_UNSUPPORTED;
+    const int grid = std::min(per_sm * num_sms(), max_grid);
+    GreedyArgs a;
+    a.n = n;
+    a.theta = theta;
+    a.set_off = set_off;
+    a.members = members;
+    a.vtx_off = vtx_off;
+    a.set_ids = set_ids;
+    a.k = k;
+    a.counts = counts;
+    a.covered = covered;
+    a.block_best = block_best;
+    a.bar = (GridBarrier *)barrier;
+    a.seeds = seeds;
+    a.gains = gains;
+    a.nseeds = nseeds;
+    a.coverage = coverage;
+    a.status = status;
+    void *args[] = {&a};
+    KernelTimer kt(st, "greedy");
+    IM_CUDA(cudaLaunchCooperativeKernel((const void *)k_greedy, dim3(grid), dim3(kGreedyThreads),
+                                        args, 0, st));
+    return IM_OK;
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_seeds,

@@ -83,6 +83,8 @@ def lib():
             "im_partition": ([i64, i32, u64, vp, vp], ctypes.c_int),
             "im_pool_sample_bytes": ([vp, vp], ctypes.c_int),
             "im_randgreedi_stats": ([vp, vp, vp], ctypes.c_int),
+            "im_max_k_cover_noalloc": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp, vp],
+                                       ctypes.c_int),
             "im_tune_set": ([i32, i64], ctypes.c_int),
             "im_tune_get": ([i32, vp], ctypes.c_int),
             "im_profile_enable": ([i32], ctypes.c_int),
@@ -227,6 +229,15 @@ def im_randgreedi_details(p, local_seeds=None, local_gains=None, local_n=None, l
 
 def im_partition(n: int, P: int, partition_seed: int, part, stream=None):
     _check(lib().im_partition(n, P, partition_seed, _ptr(part), _stream(stream)), "im_partition")
+
+
+def im_max_k_cover_noalloc(set_off, members, vtx_off, set_ids, n: int, theta: int, k: int,
+                           seeds, gains, num_seeds, coverage, stream=None):
+    """Greedy max-k-cover over caller-owned device arrays, allocating nothing."""
+    _check(lib().im_max_k_cover_noalloc(_ptr(set_off), _ptr(members), _ptr(vtx_off),
+                                        _ptr(set_ids), n, theta, k, _ptr(seeds), _ptr(gains),
+                                        _ptr(num_seeds), _ptr(coverage), _stream(stream)),
+           "im_max_k_cover_noalloc")
 
 
 def im_randgreedi_stats(p, P: int, B: int, stream=None) -> np.ndarray:
