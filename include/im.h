@@ -235,6 +235,38 @@ im_status im_max_k_cover_noalloc(const int64_t *set_off, const int32_t *members,
                                  int64_t theta, int32_t k, int32_t *seeds, int64_t *gains,
                                  int32_t *num_seeds, int64_t *coverage, void *stream);
 
+/* Grow a pool's capacity in place (contents kept; index rebuilt on demand). */
+im_status im_pool_reserve(im_pool *p, int64_t max_sets, int64_t max_entries);
+
+/* ---- IMM (Alg. 1) ------------------------------------------------------------
+ * Estimate -> martingale rounds (Sample appending to one pool, SelectSeeds,
+ * CheckGoodness) -> theta = ceil(lambda* / LB) fresh samples -> SelectSeeds.
+ * The formulas the paper defers to Tang et al. (2015) / Chen (2018), natural
+ * logs: l' = l (1 + ln 2 / ln n), e' = sqrt(2) e;
+ * lambda' = (2 + 2e'/3)(ln C(n,k) + l' ln n + ln log2 n) n / e'^2;
+ * round i = 1 .. floor(log2 n) - 1: theta_i = ceil(lambda' / (n / 2^i)), pass iff
+ * n cov / theta_i >= (1 + e') n / 2^i, LB = n cov / theta_i / (1 + e');
+ * lambda* = 2n ((1-1/e) sqrt(l' ln n + ln 2) + sqrt((1-1/e)(ln C(n,k) + l' ln n
+ * + ln 2)))^2 / e^2.  Round samples use ids 0 .. theta_last - 1, the final
+ * ones the next theta ids.  SelectSeeds follows opts (NULL: plain greedy).
+ * Outputs: seeds int32[k] (host or device), num_seeds, coverage of the final
+ * pool, theta; info (optional) records the rounds.  Pools are allocated and
+ * grown inside; IM_ERR_OOM if the RRR sets do not fit in device memory. */
+typedef struct {
+    int32_t rounds;               /* martingale rounds run */
+    int32_t reserved;
+    int64_t theta_rounds[64];     /* theta_i of each round */
+    double lb;                    /* LB (1 if no round passed) */
+    int64_t theta;                /* final theta */
+    int64_t round_entries;        /* members in the rounds' pool */
+    int64_t final_entries;        /* members in the final pool */
+    int64_t examined;             /* edges examined by the final sampling */
+} im_solve_info;
+
+im_status im_solve(const im_graph *g, im_model model, int32_t k, double eps, double ell,
+                   uint64_t seed, const im_cover_opts *opts, int32_t *seeds, int32_t *num_seeds,
+                   int64_t *coverage, int64_t *theta, im_solve_info *info, void *stream);
+
 /* Vertex partition of Alg. 3: part[v] = (Philox(v,0,0,4).x * P) >> 32. */
 im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
                        void *stream);

@@ -400,3 +400,57 @@ int orc_randgreedi(int64_t n, int64_t theta, const int64_t *set_off, const int32
     free(part); free(allowed); free(stream);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* IMM sampling-effort formulas.  Alg. 1 (Sec. 2.1) names Estimate,          */
+/* CheckGoodness and theta = f(LB) but defers their values to Tang et al.    */
+/* (SIGMOD 2015) and Chen (2018); they are written out here from that work,  */
+/* natural logs throughout:                                                  */
+/*   l' = l (1 + ln 2 / ln n),  e' = sqrt(2) e,                              */
+/*   lambda' = (2 + 2e'/3) (ln C(n,k) + l' ln n + ln log2 n) n / e'^2,        */
+/*   alpha = sqrt(l' ln n + ln 2),                                           */
+/*   beta  = sqrt((1 - 1/e) (ln C(n,k) + l' ln n + ln 2)),                   */
+/*   lambda* = 2 n ((1 - 1/e) alpha + beta)^2 / e^2,                         */
+/*   round i = 1 .. floor(log2 n) - 1: x_i = n / 2^i, theta_i = ceil(lambda'/x_i) */
+/* out: [0] l', [1] e', [2] lambda', [3] lambda*, [4] number of rounds.     */
+/* ------------------------------------------------------------------------ */
+void orc_imm_constants(int64_t n, int32_t k, double eps, double ell, double out[5]) {
+    const double dn = (double)n;
+    const double ln_n = log(dn);
+    const double lncnk = lgamma(dn + 1.0) - lgamma((double)k + 1.0) - lgamma(dn - (double)k + 1.0);
+    const double l2 = ell * (1.0 + log(2.0) / ln_n);
+    const double e2 = sqrt(2.0) * eps;
+    const double lam1 = (2.0 + 2.0 * e2 / 3.0) * (lncnk + l2 * ln_n + log(log2(dn))) * dn / (e2 * e2);
+    const double one_e = 1.0 - exp(-1.0);
+    const double alpha = sqrt(l2 * ln_n + log(2.0));
+    const double beta = sqrt(one_e * (lncnk + l2 * ln_n + log(2.0)));
+    const double lamstar = 2.0 * dn * (one_e * alpha + beta) * (one_e * alpha + beta) / (eps * eps);
+    int32_t rounds = 0;
+    while (((int64_t)1 << (rounds + 2)) <= n) ++rounds;   /* floor(log2 n) - 1 */
+    out[0] = l2;
+    out[1] = e2;
+    out[2] = lam1;
+    out[3] = lamstar;
+    out[4] = (double)rounds;
+}
+
+/* theta_i = ceil(lambda' / x_i), x_i = n / 2^i (Alg. 1's doubling theta-hat). */
+int64_t orc_imm_round_theta(double lam1, int64_t n, int32_t i) {
+    const double x = (double)n / ldexp(1.0, i);
+    return (int64_t)ceil(lam1 / x);
+}
+
+/* CheckGoodness: with F = coverage / theta_i, pass iff n F >= (1 + e') x_i;  */
+/* then LB = n F / (1 + e').  Returns 1 on pass.                             */
+int orc_imm_check(int64_t n, int64_t coverage, int64_t theta_i, int32_t i, double e2, double *lb) {
+    const double x = (double)n / ldexp(1.0, i);
+    const double spread = (double)n * ((double)coverage / (double)theta_i);
+    if (spread >= (1.0 + e2) * x) {
+        *lb = spread / (1.0 + e2);
+        return 1;
+    }
+    return 0;
+}
+
+/* Final sample count theta = ceil(lambda* / LB). */
+int64_t orc_imm_final_theta(double lamstar, double lb) { return (int64_t)ceil(lamstar / lb); }

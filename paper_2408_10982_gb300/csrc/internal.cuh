@@ -247,6 +247,9 @@ im_status pool_scratch(im_pool *p, size_t bytes, void **out);
 
 int num_sms();
 
+// imm.cu
+im_status pool_grow(im_pool *p, int64_t max_sets, int64_t max_entries, cudaStream_t st);
+
 // scan.cu
 im_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t count,
                                     const int64_t *base, void *tmp, size_t tmp_bytes,

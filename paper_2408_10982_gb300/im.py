@@ -85,6 +85,9 @@ def lib():
             "im_randgreedi_stats": ([vp, vp, vp], ctypes.c_int),
             "im_max_k_cover_noalloc": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp, vp],
                                        ctypes.c_int),
+            "im_pool_reserve": ([vp, i64, i64], ctypes.c_int),
+            "im_solve": ([vp, ctypes.c_int, i32, ctypes.c_double, ctypes.c_double, u64, vp, vp,
+                          vp, vp, vp, vp, vp], ctypes.c_int),
             "im_tune_set": ([i32, i64], ctypes.c_int),
             "im_tune_get": ([i32, vp], ctypes.c_int),
             "im_profile_enable": ([i32], ctypes.c_int),
@@ -238,6 +241,33 @@ def im_max_k_cover_noalloc(set_off, members, vtx_off, set_ids, n: int, theta: in
                                         _ptr(set_ids), n, theta, k, _ptr(seeds), _ptr(gains),
                                         _ptr(num_seeds), _ptr(coverage), _stream(stream)),
            "im_max_k_cover_noalloc")
+
+
+class SolveInfo(ctypes.Structure):
+    """im_solve_info (see include/im.h)."""
+    _fields_ = [("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("theta_rounds", ctypes.c_int64 * 64), ("lb", ctypes.c_double),
+                ("theta", ctypes.c_int64), ("round_entries", ctypes.c_int64),
+                ("final_entries", ctypes.c_int64), ("examined", ctypes.c_int64)]
+
+
+def im_pool_reserve(p, max_sets: int, max_entries: int):
+    _check(lib().im_pool_reserve(p, max_sets, max_entries), "im_pool_reserve")
+
+
+def im_solve(g, model: int, k: int, eps: float, ell: float, seed: int,
+             opts: CoverOpts | None = None, stream=None):
+    """IMM (Alg. 1) on the device path: returns (seeds, coverage, theta, info)."""
+    seeds = np.zeros(k, np.int32)
+    ns = ctypes.c_int32()
+    cov = ctypes.c_int64()
+    theta = ctypes.c_int64()
+    info = SolveInfo()
+    _check(lib().im_solve(g, model, k, eps, ell, seed,
+                          None if opts is None else ctypes.byref(opts), seeds.ctypes.data,
+                          ctypes.byref(ns), ctypes.byref(cov), ctypes.byref(theta),
+                          ctypes.byref(info), _stream(stream)), "im_solve")
+    return seeds[: ns.value].copy(), cov.value, theta.value, info
 
 
 def im_randgreedi_stats(p, P: int, B: int, stream=None) -> np.ndarray:

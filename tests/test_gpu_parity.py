@@ -270,3 +270,24 @@ def test_randgreedi_large_theta_cluster(im):
     """theta above one block's shared memory: the automatic cluster has >= 2 blocks."""
     g = inputs.rmat_graph(1 << 12, 1 << 16, 5, "lt")
     _rg_compare(im, g, im.IM_LT, 2_000_000, 40, 148, (1, 4), 0.077, False, seed=3)
+
+
+@pytest.mark.parametrize("model,wts,rg", [("ic", "trivalency", False), ("lt", "lt", False),
+                                          ("ic", "ic0.05", True)])
+def test_imm_solve_matches_oracle(im, model, wts, rg):
+    """im_solve (Alg. 1 on the device path) against the oracle's IMM driver:
+    the same theta of every round, LB, final theta, seeds and coverage."""
+    from oracle import imm as OI
+    g = inputs.rmat_graph(4096, 65536, 7, wts)
+    m = im.IM_IC if model == "ic" else im.IM_LT
+    k, eps = 10, 0.5
+    opts = im.cover_opts(im.IM_RANDGREEDI, 16, (1, 2), 0.1, 9, False) if rg else None
+    ref = OI.imm(g, O.IC if model == "ic" else O.LT, k, eps, 1.0, 42,
+                 randgreedi=(16, 9, O.trunc_count(k, 1, 2), 0.1) if rg else None)
+    G = im.Graph(g)
+    seeds, cov, theta, info = im.im_solve(G.handle, m, k, eps, 1.0, 42, opts)
+    assert list(info.theta_rounds[: info.rounds]) == ref.theta_rounds
+    assert info.lb == ref.lb
+    assert theta == ref.theta == info.theta
+    assert seeds.tolist() == ref.seeds.tolist()
+    assert cov == ref.coverage
