@@ -267,6 +267,38 @@ im_status im_solve(const im_graph *g, im_model model, int32_t k, double eps, dou
                    uint64_t seed, const im_cover_opts *opts, int32_t *seeds, int32_t *num_seeds,
                    int64_t *coverage, int64_t *theta, im_solve_info *info, void *stream);
 
+/* ---- many queries at once (batching; not in the paper) -----------------------
+ * A query: a resident graph, a model, k, theta (sample ids 0 .. theta-1) and
+ * its Philox seed.  im_solve_batch solves nq queries in a fixed number of
+ * launches (one sampling launch per model over all their samples, one sort,
+ * one covering-subset build over all queries' vertices, one greedy launch
+ * with one block per query) and gives every query exactly the seeds,
+ * gains and coverage that im_sample_rrr + im_max_k_cover (plain greedy) give
+ * it alone.  seeds int32[nq * kmax] and gains int64[nq * kmax] (row q: query
+ * q's seeds; entries past num_seeds are unspecified; gains may be NULL), host
+ * or device; res[nq] host.  An im_batch keeps its device arenas between
+ * calls (grown on demand).  Synchronises the stream. */
+typedef struct {
+    const im_graph *graph;
+    int32_t model;            /* IM_IC or IM_LT */
+    int32_t k;                /* 1 <= k <= min(kmax, n) */
+    int64_t theta;
+    uint64_t seed;
+} im_query;
+
+typedef struct {
+    int32_t num_seeds;
+    int32_t status;           /* im_status of the query */
+    int64_t coverage;
+    int64_t entries;          /* RRR set members of the query */
+} im_result;
+
+typedef struct im_batch im_batch;
+im_status im_batch_create(im_batch **out);
+im_status im_batch_destroy(im_batch *b);
+im_status im_solve_batch(im_batch *b, const im_query *q, int32_t nq, int32_t kmax, int32_t *seeds,
+                         int64_t *gains, im_result *res, void *stream);
+
 /* Vertex partition of Alg. 3: part[v] = (Philox(v,0,0,4).x * P) >> 32. */
 im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
                        void *stream);

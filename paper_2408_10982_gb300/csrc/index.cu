@@ -177,32 +177,34 @@ im_status launch_partition_labels(int64_t n, int32_t P, uint64_t pseed, int32_t 
     return IM_OK;
 }
 
+im_status build_index_raw(const int64_t *set_off, const int32_t *members, int64_t theta, int64_t T,
+                          int64_t n, int64_t *vtx_off, int32_t *set_ids, int32_t *cursor, void *tmp,
+                          cudaStream_t st) {
+    IM_CUDA(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), st));
+    if (T > 0) {
+        KernelTimer kt(st, "index_hist");
+        k_vertex_hist<<<num_sms() * 8, 256, 0, st>>>(members, T, cursor);
+    }
+    IM_CUDA(cudaGetLastError());
+    im_status s = exclusive_scan_i32_to_i64(cursor, vtx_off, n, nullptr, tmp, scan_tmp_bytes(n), st);
+    if (s != IM_OK) return s;
+    IM_CUDA(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), st));
+    if (theta > 0) {
+        KernelTimer kt(st, "index_scatter");
+        k_scatter<<<num_sms() * 8, 256, 0, st>>>(set_off, members, theta, vtx_off, cursor, set_ids);
+    }
+    IM_CUDA(cudaGetLastError());
+    return IM_OK;
+}
+
 im_status build_index(im_pool *p, cudaStream_t st) {
     if (p->index_valid) return IM_OK;
-    const int64_t n = p->g->n, T = p->total, theta = p->theta;
-    IM_CUDA(cudaMemsetAsync(p->vtx_cursor, 0, (size_t)n * sizeof(int32_t), st));
-    if (T > 0) {
-        {
-            KernelTimer kt(st, "index_hist");
-            k_vertex_hist<<<num_sms() * 8, 256, 0, st>>>(p->members, T, p->vtx_cursor);
-        }
-        IM_CUDA(cudaGetLastError());
-    }
     void *tmp = nullptr;
-    im_status s = pool_scratch(p, scan_tmp_bytes(n), &tmp);
+    im_status s = pool_scratch(p, scan_tmp_bytes(p->g->n), &tmp);
     if (s != IM_OK) return s;
-    s = exclusive_scan_i32_to_i64(p->vtx_cursor, p->vtx_off, n, nullptr, tmp, scan_tmp_bytes(n),
-                                  st);
+    s = build_index_raw(p->set_off, p->members, p->theta, p->total, p->g->n, p->vtx_off, p->set_ids,
+                        p->vtx_cursor, tmp, st);
     if (s != IM_OK) return s;
-    IM_CUDA(cudaMemsetAsync(p->vtx_cursor, 0, (size_t)n * sizeof(int32_t), st));
-    if (theta > 0) {
-        {
-            KernelTimer kt(st, "index_scatter");
-            k_scatter<<<num_sms() * 8, 256, 0, st>>>(p->set_off, p->members, theta, p->vtx_off,
-                                                     p->vtx_cursor, p->set_ids);
-        }
-        IM_CUDA(cudaGetLastError());
-    }
     p->index_valid = true;
     return IM_OK;
 }

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
+#include <vector>
 
 #include "../../include/im.h"
 
@@ -150,6 +152,20 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 
 }  // namespace im
 
+// What a sampling kernel needs of one query: its graph and random stream.
+// A launch reads a table of these; a single-query launch has one entry.
+struct QueryView {
+    const int64_t *in_off;
+    const int32_t *in_src;
+    const uint32_t *w;
+    const uint4 *lt_vrec;
+    const unsigned long long *lt_leaf;
+    const unsigned long long *lt_tree;
+    uint64_t seed;
+    uint32_t n;
+    uint32_t first;      // sample id of the query's first sample
+};
+
 // ---------------------------------------------------------------------------
 // handle layouts (host side)
 // ---------------------------------------------------------------------------
@@ -257,12 +273,41 @@ im_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t cou
 size_t scan_tmp_bytes(int64_t count);
 
 // sample.cu
+// One sampling launch of one model over a table of queries: query q draws
+// counts[q] samples (ids first_q ..) into stage[]; sizes / stage_off are
+// indexed by the flattened sample index.  Scratch comes from `alloc`.
+struct SamplingJob {
+    im_model model;
+    std::vector<QueryView> views;
+    std::vector<int64_t> counts;
+    int64_t n_max;
+    int32_t *stage;
+    int64_t stage_cap;
+};
+struct SamplingResult {
+    int64_t *stage_off;      // [total]
+    int32_t *sizes;          // [total]
+    void *scan_tmp;          // scan_tmp_bytes(total) bytes
+    void *sort_tmp;          // (2 + 2 total) * 8 bytes
+    int64_t total;           // samples
+    int64_t added;           // members written to the stage
+    int64_t examined;
+    int64_t alg_bytes;
+};
+im_status run_sampling(const SamplingJob &job, const std::function<im_status(size_t, void **)> &alloc,
+                       cudaStream_t st, SamplingResult *res);
+im_status segmented_sort_sets(int32_t *dst, const int64_t *seg_off, int64_t nseg, const int32_t *stage,
+                              const int64_t *stage_off, void *tmp, int64_t n_max, cudaStream_t st);
+QueryView query_view(const im_graph *g, uint64_t seed, uint64_t first);
 im_status sample_append(const im_graph *g, im_model model, uint64_t seed, uint64_t first,
                         uint64_t count, im_pool *pool, cudaStream_t st);
 im_status build_lt_index(im_graph *g, cudaStream_t st);
 
 // index.cu
 im_status build_index(im_pool *p, cudaStream_t st);
+im_status build_index_raw(const int64_t *set_off, const int32_t *members, int64_t theta, int64_t T,
+                          int64_t n, int64_t *vtx_off, int32_t *set_ids, int32_t *cursor, void *tmp,
+                          cudaStream_t st);
 im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st);
 im_status launch_partition_labels(int64_t n, int32_t P, uint64_t pseed, int32_t *part,
                                   cudaStream_t st);

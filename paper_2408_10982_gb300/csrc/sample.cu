@@ -30,15 +30,9 @@ constexpr int kWarpSortBytes = 4096;         // per-warp smem sort buffer
 constexpr int kBlockSortCap = 16384;         // ... by one block in shared memory (int32)
 
 struct SampleArgs {
-    uint32_t n;
-    const int64_t *in_off;
-    const int32_t *in_src;
-    const uint32_t *w;
-    const uint4 *lt_vrec;             // per vertex {edge offset, in-degree, tree offset, 0}
-    const unsigned long long *lt_leaf;  // per edge: cumulative weight << 31 | source
-    const unsigned long long *lt_tree;  // per vertex: upper levels of the search tree
-    uint64_t seed;
-    uint32_t first;
+    const QueryView *qv;      // [nq] graphs and streams of the queries of this launch
+    const int64_t *qstart;    // [nq + 1] first flattened sample index of each query
+    int32_t nq;
     int64_t count;            // work items
     const int64_t *list;      // if non-null: work item i is sample index list[i]
     int32_t *stage;
@@ -57,6 +51,17 @@ struct SampleArgs {
     unsigned long long *ovf_count;
     int *status;
 };
+
+// The query that flattened sample index j belongs to (largest q, qstart[q] <= j).
+__device__ __forceinline__ int find_query(const SampleArgs &a, int64_t j) {
+    int lo = 0, hi = a.nq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(a.qstart + mid) <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ int64_t next_item(const SampleArgs &a, int lane) {
     unsigned long long j = 0;
@@ -111,13 +116,19 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
     if (kSmemVis)
         for (int64_t i = lane; i < a.vis_words; i += 32) vis[i] = 0;
     __syncwarp();
-    const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
     unsigned long long exam = 0, abytes = 0;
     for (;;) {
         const int64_t j = next_item(a, lane);
         if (j < 0) break;
-        const uint32_t s = a.first + (uint32_t)j;
-        const uint32_t root = rrr_root(a.seed, s, a.n);
+        const int qi = find_query(a, j);
+        const QueryView &V = a.qv[qi];
+        const int64_t *in_off = V.in_off;
+        const int32_t *in_src = V.in_src;
+        const uint32_t *wgt = V.w;
+        const uint64_t seed = V.seed;
+        const uint32_t k0 = seed_lo(seed), k1 = seed_hi(seed);
+        const uint32_t s = V.first + (uint32_t)(j - __ldg(a.qstart + qi));
+        const uint32_t root = rrr_root(seed, s, V.n);
         if (lane == 0) {
             atomicOr(&vis[root >> 5], 1u << (root & 31));
             q[0] = (int32_t)root;
@@ -131,8 +142,8 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
             int64_t eb = 0, ee = 0;
             if (lane < nb) {
                 const int32_t v = q[head + lane];
-                eb = __ldg(a.in_off + v);
-                ee = __ldg(a.in_off + v + 1);
+                eb = __ldg(in_off + v);
+                ee = __ldg(in_off + v + 1);
                 sexam += (unsigned long long)(ee - eb);
             }
             head += nb;
@@ -160,8 +171,8 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
                     const uint4 coin = philox4x32_10(
                         make_uint4(s, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), kStreamCoin), k0,
                         k1);
-                    const uint4 wv = __ldg(reinterpret_cast<const uint4 *>(a.w) + g);
-                    const int4 sv = __ldg(reinterpret_cast<const int4 *>(a.in_src) + g);
+                    const uint4 wv = __ldg(reinterpret_cast<const uint4 *>(wgt) + g);
+                    const int4 sv = __ldg(reinterpret_cast<const int4 *>(in_src) + g);
                     const uint32_t cv[4] = {coin.x, coin.y, coin.z, coin.w};
                     const uint32_t wq[4] = {wv.x, wv.y, wv.z, wv.w};
                     src[0] = sv.x; src[1] = sv.y; src[2] = sv.z; src[3] = sv.w;
@@ -251,7 +262,7 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 // search tree is a window of up to 32 values; lane l of a group holds values
 // [l * 32/G, (l + 1) * 32/G) of it.
 template <int G>
-__global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 6) k_sample_lt(SampleArgs a) {
+__global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(SampleArgs a) {
     constexpr int NG = 32 / G;                       // walks per warp
     constexpr int NV = 32 / G;                       // window values per lane
     constexpr int PS = G == 32 ? kPathSmem : kPathSmemGroup;
@@ -263,11 +274,12 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 6) k_sample_lt(S
     const int64_t slot = ((int64_t)blockIdx.x * kWarps + wib) * NG + grp;
     int32_t *q = a.queues + (size_t)slot * (size_t)a.qcap;
     int32_t *sp = spath[wib * NG + grp];
-    const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
     unsigned long long exam = 0, abytes = 0;
     bool active = false, exhausted = false;
     int64_t j = 0;
-    uint32_t s = 0, cur = 0;
+    uint32_t s = 0, cur = 0, k0 = 0, k1 = 0;
+    const uint4 *vrec = nullptr;
+    const unsigned long long *leaf_arr = nullptr, *tree = nullptr;
     int32_t len = 0;
     unsigned long long sexam = 0;
     uint32_t sbytes = 0;   // flushed into abytes before it can wrap
@@ -278,8 +290,15 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 6) k_sample_lt(S
             jw = __shfl_sync(gmask, jw, 0, G);
             if (jw < (unsigned long long)a.count) {
                 j = a.list ? a.list[jw] : (int64_t)jw;
-                s = a.first + (uint32_t)j;
-                cur = rrr_root(a.seed, s, a.n);
+                const int qi = find_query(a, j);
+                const QueryView &V = a.qv[qi];
+                vrec = V.lt_vrec;
+                leaf_arr = V.lt_leaf;
+                tree = V.lt_tree;
+                k0 = seed_lo(V.seed);
+                k1 = seed_hi(V.seed);
+                s = V.first + (uint32_t)(j - __ldg(a.qstart + qi));
+                cur = rrr_root(V.seed, s, V.n);
                 if (gl == 0) {
                     q[0] = (int32_t)cur;
                     sp[0] = (int32_t)cur;
@@ -298,11 +317,11 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 6) k_sample_lt(S
         // ---- one step of every active walk ----
         const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
         const unsigned long long xs = (unsigned long long)x;
-        const uint4 vr = active ? __ldg(a.lt_vrec + cur) : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 vr = active ? __ldg(vrec + cur) : make_uint4(0u, 0u, 0u, 0u);
         const int32_t d = (int32_t)vr.y;
         bool live = active && d > 0;                 // group-uniform
         const int lmax = (int)__reduce_max_sync(kFull, live ? vr.w : 0u);
-        const unsigned long long *lvl = a.lt_tree + vr.z;   // levels stored top-down
+        const unsigned long long *lvl = tree + vr.z;   // levels stored top-down
         int32_t blk = 0;
         for (int l = lmax; l >= 1; --l) {
             const bool here = live && l <= (int)vr.w;
@@ -333,7 +352,7 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 6) k_sample_lt(S
             for (int v = NV - 1; v >= 0; --v) {
                 const int32_t idx = blk * 32 + gl * NV + v;
                 if (live && idx < d) {
-                    const unsigned long long r = __ldg(a.lt_leaf + vr.x + idx);
+                    const unsigned long long r = __ldg(leaf_arr + vr.x + idx);
                     if (xs < (r >> 31)) {
                         lf = v;
                         hit = r;
@@ -721,27 +740,31 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
     return IM_OK;
 }
 
+QueryView query_view(const im_graph *g, uint64_t seed, uint64_t first) {
+    QueryView v;
+    v.in_off = g->in_off;
+    v.in_src = g->in_src;
+    v.w = g->w;
+    v.lt_vrec = g->lt_vrec;
+    v.lt_leaf = g->lt_leaf;
+    v.lt_tree = g->lt_tree;
+    v.seed = seed;
+    v.n = (uint32_t)g->n;
+    v.first = (uint32_t)first;
+    return v;
+}
+
 // ---------------------------------------------------------------------------
-// Sample(G, count): append sample ids first .. first+count-1 to the pool.
+// One sampling launch over a table of queries (see SamplingJob).
 // ---------------------------------------------------------------------------
-im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint64_t first,
-                        uint64_t count, im_pool *pool, cudaStream_t st) {
-    im_graph *g = const_cast<im_graph *>(gc);
-    if (model == IM_LT) {
-        im_status s = build_lt_index(g, st);
-        if (s != IM_OK) return s;
-        if (!g->lt_valid) {
-            set_error("LT sampling needs every vertex's in-weights to sum to at most 2^32");
-            return IM_ERR_INVALID_ARG;
-        }
-    }
-    if (count == 0) return IM_OK;
-    if (pool->theta + (int64_t)count > pool->max_sets) {
-        set_error("pool max_sets exceeded");
-        return IM_ERR_CAPACITY;
-    }
-    const int64_t cnt = (int64_t)count;
-    const int64_t n = g->n;
+im_status run_sampling(const SamplingJob &job, const std::function<im_status(size_t, void **)> &alloc,
+                       cudaStream_t st, SamplingResult *res) {
+    const im_model model = job.model;
+    const int32_t nq = (int32_t)job.views.size();
+    std::vector<int64_t> qstart(nq + 1, 0);
+    for (int32_t q = 0; q < nq; ++q) qstart[q + 1] = qstart[q] + job.counts[q];
+    const int64_t cnt = qstart[nq];
+    const int64_t n = job.n_max;
     const bool smem_vis = model == IM_IC && n <= kSmemVisBits;
     const int64_t vis_words = (n + 31) / 32;
 
@@ -758,10 +781,10 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
         IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)dyn_smem));
     int blocks = blocks_for(kern, kSampleThreads, dyn_smem);
-    // global visited bitmaps are n bits per warp: keep them within ~4 GB
+    // global visited bitmaps are n bits per warp: keep them within ~2 GB
     if (model == IM_IC && !smem_vis) {
         int64_t cap_blocks = std::max<int64_t>(
-            num_sms(), (int64_t)(4ll << 30) / ((int64_t)kWarps * vis_words * 4));
+            num_sms(), (int64_t)(2ll << 30) / ((int64_t)kWarps * vis_words * 4));
         blocks = (int)std::min<int64_t>(blocks, cap_blocks);
     }
     const int64_t warps = (int64_t)blocks * kWarps;
@@ -776,6 +799,8 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
         return at;
     };
     const size_t o_ctr = take(8 * sizeof(unsigned long long));
+    const size_t o_views = take((size_t)nq * sizeof(QueryView));
+    const size_t o_qstart = take((size_t)(nq + 1) * 8);
     const size_t o_soff = take((size_t)cnt * 8);
     const size_t o_sizes = take((size_t)cnt * 4);
     const size_t o_ovf = take((size_t)cnt * 8);
@@ -784,30 +809,28 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     const size_t o_q = take((size_t)slots * qcap * 4);
     const size_t o_vis = take(model == IM_IC && !smem_vis ? (size_t)warps * vis_words * 4 : 0);
     void *base = nullptr;
-    im_status rs = pool_scratch(pool, off, &base);
+    im_status rs = alloc(off, &base);
     if (rs != IM_OK) return rs;
     char *B = (char *)base;
     unsigned long long *ctr = (unsigned long long *)(B + o_ctr);
     // ctr: 0 work, 1 stage cursor, 2 examined, 3 overflow count, 4 status (int),
     //      5 algorithmic bytes
     IM_CUDA(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), st));
+    IM_CUDA(cudaMemcpyAsync(B + o_views, job.views.data(), (size_t)nq * sizeof(QueryView),
+                            cudaMemcpyHostToDevice, st));
+    IM_CUDA(cudaMemcpyAsync(B + o_qstart, qstart.data(), (size_t)(nq + 1) * 8,
+                            cudaMemcpyHostToDevice, st));
     if (o_vis && model == IM_IC && !smem_vis)
         IM_CUDA(cudaMemsetAsync(B + o_vis, 0, (size_t)warps * vis_words * 4, st));
 
     SampleArgs a;
-    a.n = (uint32_t)n;
-    a.in_off = g->in_off;
-    a.in_src = g->in_src;
-    a.w = g->w;
-    a.lt_vrec = g->lt_vrec;
-    a.lt_leaf = g->lt_leaf;
-    a.lt_tree = g->lt_tree;
-    a.seed = seed;
-    a.first = (uint32_t)first;
+    a.qv = (const QueryView *)(B + o_views);
+    a.qstart = (const int64_t *)(B + o_qstart);
+    a.nq = nq;
     a.count = cnt;
     a.list = nullptr;
-    a.stage = pool->set_ids;                      // the index buffer doubles as the stage
-    a.stage_cap = pool->max_entries - pool->total;
+    a.stage = job.stage;
+    a.stage_cap = job.stage_cap;
     a.stage_cursor = ctr + 1;
     a.stage_off = (int64_t *)(B + o_soff);
     a.sizes = (int32_t *)(B + o_sizes);
@@ -821,7 +844,6 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     a.ovf_list = (int64_t *)(B + o_ovf);
     a.ovf_count = ctr + 3;
     a.status = (int *)(ctr + 4);
-    pool->index_valid = false;
 
     auto launch = [&](int nblocks, int group) {
         KernelTimer kt(st, model == IM_LT ? "sample_lt" : "sample_ic");
@@ -843,7 +865,7 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     IM_CUDA(cudaStreamSynchronize(st));
     int dev_status = (int)(hc[4] & 0xffffffffu);
     if (dev_status == kDevOk && hc[3] > 0 && qcap < n) {
-        // second pass for sets longer than the per-warp queue: a few warps
+        // second pass for sets longer than the per-walk queue: a few warps
         // with queues of n entries re-run exactly those samples
         const int64_t novf = (int64_t)hc[3];
         int nb2 = (int)std::max<int64_t>(1, std::min<int64_t>((novf + kWarps - 1) / kWarps,
@@ -874,43 +896,95 @@ im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint6
     }
     if (dev_status != kDevOk) {
         if (dev_status == kDevStageOverflow) {
-            set_error("pool max_entries exceeded while sampling");
+            set_error("RRR set capacity exceeded while sampling");
             return IM_ERR_CAPACITY;
         }
         return map_dev_status(dev_status, "sampling");
     }
-    const int64_t added = (int64_t)hc[1];
+    res->stage_off = (int64_t *)(B + o_soff);
+    res->sizes = (int32_t *)(B + o_sizes);
+    res->scan_tmp = B + o_scan;
+    res->sort_tmp = B + o_sort;
+    res->total = cnt;
+    res->added = (int64_t)hc[1];
+    res->examined = (int64_t)hc[2];
+    res->alg_bytes = (int64_t)hc[5];
+    return IM_OK;
+}
 
-    // set_off[theta .. theta+cnt] = set_off[theta] + exclusive scan of sizes
-    int64_t *so = pool->set_off + pool->theta;
-    rs = exclusive_scan_i32_to_i64(a.sizes, so, cnt, so, B + o_scan, scan_tmp_bytes(cnt), st);
-    if (rs != IM_OK) return rs;
-    // copy stage -> members and sort each set ascending
+// Copies every set from the stage into dst at seg_off and sorts it ascending.
+im_status segmented_sort_sets(int32_t *dst, const int64_t *seg_off, int64_t nseg, const int32_t *stage,
+                              const int64_t *stage_off, void *tmp, int64_t n_max, cudaStream_t st) {
     int64_t ngiant = 0;
-    uint32_t *gbm = nullptr;
-    const int64_t gwords = vis_words;
-    // giant sets (> block sort cap) need an n-bit bitmap per block
-    rs = segmented_sort_impl<int32_t>(pool->members, so, cnt, a.stage, a.stage_off, B + o_sort,
-                                      (size_t)(2 + 2 * cnt) * 8, &ngiant, st, "sort_sets_warp",
-                                      "sort_sets_block");
+    im_status rs = segmented_sort_impl<int32_t>(dst, seg_off, nseg, stage, stage_off, tmp,
+                                                (size_t)(2 + 2 * nseg) * 8, &ngiant, st,
+                                                "sort_sets_warp", "sort_sets_block");
     if (rs != IM_OK) return rs;
     if (ngiant > 0) {
+        // giant sets (> block sort cap) need an n-bit bitmap per block
+        const int64_t gwords = (n_max + 31) / 32;
         const int blocks3 = (int)std::min<int64_t>(ngiant, num_sms());
+        uint32_t *gbm = nullptr;
         IM_CUDA(cudaMallocAsync((void **)&gbm, (size_t)blocks3 * gwords * 4, st));
         IM_CUDA(cudaMemsetAsync(gbm, 0, (size_t)blocks3 * gwords * 4, st));
-        unsigned long long *sctr = (unsigned long long *)(B + o_sort);
-        int64_t *giant = (int64_t *)(B + o_sort) + 2 + cnt;
+        unsigned long long *sctr = (unsigned long long *)tmp;
+        int64_t *giant = (int64_t *)tmp + 2 + nseg;
         {
             KernelTimer kt(st, "sort_sets_bitmap");
-            k_sort_giant<<<blocks3, 1024, 0, st>>>(pool->members, so, giant, sctr + 1, gbm, gwords);
+            k_sort_giant<<<blocks3, 1024, 0, st>>>(dst, seg_off, giant, sctr + 1, gbm, gwords);
         }
         IM_CUDA(cudaGetLastError());
         IM_CUDA(cudaFreeAsync(gbm, st));
     }
+    return IM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sample(G, count): append sample ids first .. first+count-1 to the pool.
+// ---------------------------------------------------------------------------
+im_status sample_append(const im_graph *gc, im_model model, uint64_t seed, uint64_t first,
+                        uint64_t count, im_pool *pool, cudaStream_t st) {
+    im_graph *g = const_cast<im_graph *>(gc);
+    if (model == IM_LT) {
+        im_status s = build_lt_index(g, st);
+        if (s != IM_OK) return s;
+        if (!g->lt_valid) {
+            set_error("LT sampling needs every vertex's in-weights to sum to at most 2^32");
+            return IM_ERR_INVALID_ARG;
+        }
+    }
+    if (count == 0) return IM_OK;
+    if (pool->theta + (int64_t)count > pool->max_sets) {
+        set_error("pool max_sets exceeded");
+        return IM_ERR_CAPACITY;
+    }
+    const int64_t cnt = (int64_t)count;
+    SamplingJob job;
+    job.model = model;
+    job.views.push_back(query_view(g, seed, first));
+    job.counts.push_back(cnt);
+    job.n_max = g->n;
+    job.stage = pool->set_ids;                      // the index buffer doubles as the stage
+    job.stage_cap = pool->max_entries - pool->total;
+    pool->index_valid = false;
+    SamplingResult r;
+    im_status rs = run_sampling(job, [&](size_t b, void **p) { return pool_scratch(pool, b, p); },
+                                st, &r);
+    if (rs != IM_OK) {
+        if (rs == IM_ERR_CAPACITY) set_error("pool max_entries exceeded while sampling");
+        return rs;
+    }
+    // set_off[theta .. theta+cnt] = set_off[theta] + exclusive scan of sizes
+    int64_t *so = pool->set_off + pool->theta;
+    rs = exclusive_scan_i32_to_i64(r.sizes, so, cnt, so, r.scan_tmp, scan_tmp_bytes(cnt), st);
+    if (rs != IM_OK) return rs;
+    // copy stage -> members and sort each set ascending
+    rs = segmented_sort_sets(pool->members, so, cnt, job.stage, r.stage_off, r.sort_tmp, g->n, st);
+    if (rs != IM_OK) return rs;
     pool->theta += cnt;
-    pool->total += added;
-    pool->examined += (int64_t)hc[2];
-    pool->sample_bytes += (int64_t)hc[5];
+    pool->total += r.added;
+    pool->examined += r.examined;
+    pool->sample_bytes += r.alg_bytes;
     IM_CUDA(cudaStreamSynchronize(st));
     return IM_OK;
 }

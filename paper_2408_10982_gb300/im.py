@@ -86,6 +86,9 @@ def lib():
             "im_max_k_cover_noalloc": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp, vp],
                                        ctypes.c_int),
             "im_pool_reserve": ([vp, i64, i64], ctypes.c_int),
+            "im_batch_create": ([pp], ctypes.c_int),
+            "im_batch_destroy": ([vp], ctypes.c_int),
+            "im_solve_batch": ([vp, vp, i32, i32, vp, vp, vp, vp], ctypes.c_int),
             "im_solve": ([vp, ctypes.c_int, i32, ctypes.c_double, ctypes.c_double, u64, vp, vp,
                           vp, vp, vp, vp, vp], ctypes.c_int),
             "im_tune_set": ([i32, i64], ctypes.c_int),
@@ -249,6 +252,47 @@ class SolveInfo(ctypes.Structure):
                 ("theta_rounds", ctypes.c_int64 * 64), ("lb", ctypes.c_double),
                 ("theta", ctypes.c_int64), ("round_entries", ctypes.c_int64),
                 ("final_entries", ctypes.c_int64), ("examined", ctypes.c_int64)]
+
+
+class Query(ctypes.Structure):
+    """im_query (see include/im.h)."""
+    _fields_ = [("graph", ctypes.c_void_p), ("model", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("theta", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    """im_result (see include/im.h)."""
+    _fields_ = [("num_seeds", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("coverage", ctypes.c_int64), ("entries", ctypes.c_int64)]
+
+
+def im_batch_create():
+    h = ctypes.c_void_p()
+    _check(lib().im_batch_create(ctypes.byref(h)), "im_batch_create")
+    return h
+
+
+def im_batch_destroy(b):
+    _check(lib().im_batch_destroy(b), "im_batch_destroy")
+
+
+def im_solve_batch(b, queries, kmax: int, stream=None):
+    """queries: list of (graph handle, model, k, theta, seed).  Returns a list of
+    (seeds, gains, coverage, entries) per query."""
+    nq = len(queries)
+    arr = (Query * nq)(*[Query(g.value if hasattr(g, "value") else g, m, k, th, sd)
+                         for g, m, k, th, sd in queries])
+    seeds = np.zeros(nq * kmax, np.int32)
+    gains = np.zeros(nq * kmax, np.int64)
+    res = (Result * nq)()
+    _check(lib().im_solve_batch(b, arr, nq, kmax, seeds.ctypes.data, gains.ctypes.data, res,
+                                _stream(stream)), "im_solve_batch")
+    out = []
+    for q in range(nq):
+        m = res[q].num_seeds
+        out.append((seeds[q * kmax:q * kmax + m].copy(), gains[q * kmax:q * kmax + m].copy(),
+                    res[q].coverage, res[q].entries))
+    return out
 
 
 def im_pool_reserve(p, max_sets: int, max_entries: int):

@@ -291,3 +291,38 @@ def test_imm_solve_matches_oracle(im, model, wts, rg):
     assert theta == ref.theta == info.theta
     assert seeds.tolist() == ref.seeds.tolist()
     assert cov == ref.coverage
+
+
+def test_solve_batch_matches_oracle_and_single_path(im):
+    """A mixed batch (graphs of several sizes, IC and LT, uneven k and theta):
+    every query gets the oracle's seeds, gains and coverage -- the same as alone."""
+    graphs = {
+        "a": inputs.rmat_graph(1 << 12, 1 << 16, 1, "ic0.1"),
+        "b": inputs.rmat_graph(1 << 13, 1 << 17, 2, "lt"),
+        "c": inputs.random_graph(50, 300, 3, "0.3"),
+        "d": inputs.rmat_graph(1 << 17, 1 << 21, 4, "lt"),
+    }
+    G = {k: im.Graph(g) for k, g in graphs.items()}
+    rng = np.random.default_rng(0)
+    queries = []
+    for q in range(23):
+        name = "abcd"[q % 4]
+        g = graphs[name]
+        model = im.IM_LT if name in "bd" else im.IM_IC
+        k = int(rng.integers(1, min(40, g.n) + 1))
+        theta = int(rng.integers(0, 6000)) if q % 5 else 1
+        queries.append((name, model, k, theta, int(rng.integers(0, 2**62))))
+    batch = im.im_batch_create()
+    try:
+        for _ in range(2):                    # the arenas are reused on the second call
+            out = im.im_solve_batch(batch, [(G[n].handle, m, k, th, sd)
+                                            for n, m, k, th, sd in queries], 40)
+            for (name, m, k, th, sd), (seeds, gains, cov, entries) in zip(queries, out):
+                g = graphs[name]
+                pool = O.sample(O.IC if m == im.IM_IC else O.LT, g, sd, 0, th)
+                rc = O.greedy(g.n, pool, O.invert(g.n, pool), k)
+                assert seeds.tolist() == rc.seeds.tolist(), (name, k, th)
+                assert gains.tolist() == rc.gains.tolist()
+                assert cov == rc.coverage and entries == pool.members.size
+    finally:
+        im.im_batch_destroy(batch)
