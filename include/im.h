@@ -299,6 +299,38 @@ im_status im_batch_destroy(im_batch *b);
 im_status im_solve_batch(im_batch *b, const im_query *q, int32_t nq, int32_t kmax, int32_t *seeds,
                          int64_t *gains, im_result *res, void *stream);
 
+/* ---- serving (not in the paper) ------------------------------------------------
+ * A request loop with continuous batching over resident graphs: workers (each
+ * with its own stream and batch arena) take queued requests in arrival order,
+ * admit as many as max_batch and the device-memory budget allow (footprint
+ * estimated from theta and the members per set seen so far on the request's
+ * graph and model; a worker with nothing in flight always admits one), run
+ * them through im_solve_batch and publish the results.  Requests arriving
+ * while batches run join the next batch; with workers > 1 batches overlap on
+ * the device.  Every result equals the query's result alone. */
+typedef struct {
+    int32_t workers;          /* batches in flight at once, 1..16 */
+    int32_t max_batch;        /* requests per batch, >= 1 */
+    int64_t mem_budget;       /* device bytes the in-flight batches may use */
+} im_server_opts;
+
+typedef struct im_server im_server;
+im_status im_server_create(const im_server_opts *opts, im_server **out);
+/* Finishes every queued request, then stops the workers. */
+im_status im_server_destroy(im_server *s);
+/* Queues a query (copied); *ticket identifies it.  The graph must stay alive. */
+im_status im_server_submit(im_server *s, const im_query *q, uint64_t *ticket);
+/* Result of a finished request, then forgotten: seeds int32[k] (host), number
+ * of seeds, coverage, and the latency from submission to completion.
+ * IM_ERR_BUSY while the request is queued or running. */
+im_status im_server_poll(im_server *s, uint64_t ticket, int32_t *seeds, int32_t *num_seeds,
+                         int64_t *coverage, double *latency_ms);
+/* As im_server_poll, blocking up to timeout_s seconds (IM_ERR_BUSY on timeout). */
+im_status im_server_wait(im_server *s, uint64_t ticket, double timeout_s, int32_t *seeds,
+                         int32_t *num_seeds, int64_t *coverage, double *latency_ms);
+/* Batches run, requests they held, requests still queued. */
+im_status im_server_stats(im_server *s, int64_t *batches, int64_t *queries, int64_t *queued);
+
 /* Vertex partition of Alg. 3: part[v] = (Philox(v,0,0,4).x * P) >> 32. */
 im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
                        void *stream);

@@ -12,6 +12,7 @@
 // 32-ary search over the per-vertex cumulative weights, the revisit test is a
 // warp compare against the path held in shared memory.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -700,7 +701,10 @@ im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, c
     return IM_OK;
 }
 
+static std::mutex g_lt_index_mu;   // graphs are shared by serving workers
+
 im_status build_lt_index(im_graph *g, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_lt_index_mu);
     if (g->lt_leaf) return IM_OK;
     const int64_t n = g->n, m = g->m;
     int32_t *sizes = nullptr;

@@ -1,0 +1,253 @@
+// server.cu -- request loop with continuous batching over resident graphs.
+//
+// Clients submit queries (im_server_submit) and poll or wait for their
+// results.  Worker threads -- each with its own CUDA stream and im_batch
+// arena -- take the queued requests in arrival order, admit as many as the
+// batch size and the device-memory budget allow (a request's footprint is
+// estimated from theta and the members per set seen so far on its graph and
+// model), solve them with im_solve_batch, and publish the results.  Requests
+// that arrive while batches are on the GPU wait for the next free worker;
+// with several workers, batches overlap on the device.  A result does not
+// depend on the batch it ran in.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    im_query q;
+    Clock::time_point submitted, finished;
+    int64_t footprint = 0;
+    bool done = false;
+    im_status status = IM_OK;
+    std::vector<int32_t> seeds;
+    int64_t coverage = 0;
+    int64_t entries = 0;
+};
+
+}  // namespace
+
+struct im_server {
+    int device = 0;
+    im_server_opts opts;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, Request> reqs;
+    std::map<std::pair<const im_graph *, int32_t>, double> per_set;   // members per set seen
+    std::vector<std::thread> workers;
+    int64_t mem_in_use = 0;
+    int32_t in_flight = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    // counters
+    int64_t batches = 0, batched_queries = 0;
+};
+
+namespace {
+
+// device bytes a request needs inside a batch: stage + members + covering
+// subsets (12 B per member), set offsets and sizes (20 B per set), the
+// covered bitmap, and per-vertex greedy state (24 B per vertex)
+int64_t footprint(im_server *s, const im_query &q) {
+    auto it = s->per_set.find({q.graph, q.model});
+    const double per = it != s->per_set.end() ? it->second : 64.0;
+    return (int64_t)((double)q.theta * per * 1.5 * 12.0) + q.theta * 20 + q.theta / 8 +
+           q.graph->n * 24 + 4096;
+}
+
+void worker_main(im_server *s) {
+    cudaSetDevice(s->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    im_batch *b = nullptr;
+    im_batch_create(&b);
+    std::vector<uint64_t> ids;
+    std::vector<im_query> qs;
+    for (;;) {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv_work.wait(lk, [&] {
+            if (s->stop && s->queue.empty()) return true;
+            if (s->queue.empty()) return false;
+            const Request &r = s->reqs[s->queue.front()];
+            return s->in_flight == 0 || s->mem_in_use + r.footprint <= s->opts.mem_budget;
+        });
+        if (s->queue.empty()) break;   // stop requested and nothing left
+        // admit in arrival order while the batch and the memory budget allow
+        ids.clear();
+        qs.clear();
+        int64_t mem = 0;
+        while (!s->queue.empty() && (int32_t)ids.size() < s->opts.max_batch) {
+            const uint64_t t = s->queue.front();
+            Request &r = s->reqs[t];
+            if (!ids.empty() && s->mem_in_use + mem + r.footprint > s->opts.mem_budget) break;
+            mem += r.footprint;
+            ids.push_back(t);
+            qs.push_back(r.q);
+            s->queue.pop_front();
+        }
+        s->mem_in_use += mem;
+        s->in_flight++;
+        lk.unlock();
+
+        int32_t kmax = 1;
+        for (auto &q : qs) kmax = std::max(kmax, q.k);
+        std::vector<int32_t> seeds((size_t)qs.size() * kmax);
+        std::vector<im_result> res(qs.size());
+        const im_status st_batch =
+            im_solve_batch(b, qs.data(), (int32_t)qs.size(), kmax, seeds.data(), nullptr, res.data(), st);
+        const auto now = Clock::now();
+
+        lk.lock();
+        for (size_t i = 0; i < ids.size(); ++i) {
+            Request &r = s->reqs[ids[i]];
+            r.done = true;
+            r.finished = now;
+            r.status = st_batch;
+            if (st_batch == IM_OK) {
+                r.seeds.assign(seeds.begin() + (int64_t)i * kmax,
+                               seeds.begin() + (int64_t)i * kmax + res[i].num_seeds);
+                r.coverage = res[i].coverage;
+                r.entries = res[i].entries;
+                if (r.q.theta > 0) {
+                    double &est = s->per_set[{r.q.graph, r.q.model}];
+                    const double seen = (double)res[i].entries / (double)r.q.theta;
+                    est = est > 0 ? 0.5 * est + 0.5 * seen : seen;
+                }
+            }
+        }
+        s->batches++;
+        s->batched_queries += (int64_t)ids.size();
+        s->mem_in_use -= mem;
+        s->in_flight--;
+        lk.unlock();
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+    im_batch_destroy(b);
+    cudaStreamDestroy(st);
+}
+
+im_status take_result(im_server *s, uint64_t ticket, int32_t *seeds, int32_t *num_seeds,
+                      int64_t *coverage, double *latency_ms, std::unique_lock<std::mutex> &lk) {
+    auto it = s->reqs.find(ticket);
+    Request &r = it->second;
+    const im_status st = r.status;
+    if (st == IM_OK) {
+        if (seeds && !r.seeds.empty()) std::memcpy(seeds, r.seeds.data(), r.seeds.size() * 4);
+        if (num_seeds) *num_seeds = (int32_t)r.seeds.size();
+        if (coverage) *coverage = r.coverage;
+    }
+    if (latency_ms)
+        *latency_ms = std::chrono::duration<double, std::milli>(r.finished - r.submitted).count();
+    s->reqs.erase(it);
+    (void)lk;
+    return st;
+}
+
+}  // namespace
+
+using namespace im;
+
+extern "C" {
+
+im_status im_server_create(const im_server_opts *opts, im_server **out) {
+    if (!opts || !out || opts->workers < 1 || opts->workers > 16 || opts->max_batch < 1 ||
+        opts->mem_budget <= 0) {
+        set_error("im_server_create: bad options");
+        return IM_ERR_INVALID_ARG;
+    }
+    im_server *s = new (std::nothrow) im_server();
+    if (!s) return IM_ERR_OOM;
+    s->opts = *opts;
+    cudaGetDevice(&s->device);
+    for (int32_t w = 0; w < opts->workers; ++w) s->workers.emplace_back(worker_main, s);
+    *out = s;
+    return IM_OK;
+}
+
+im_status im_server_destroy(im_server *s) {
+    if (!s) return IM_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto &t : s->workers) t.join();
+    delete s;
+    return IM_OK;
+}
+
+im_status im_server_submit(im_server *s, const im_query *q, uint64_t *ticket) {
+    if (!s || !q || !ticket || !q->graph || q->k < 1 || q->k > q->graph->n || q->theta < 0 ||
+        (q->model != IM_IC && q->model != IM_LT) || q->graph->device != s->device) {
+        set_error("im_server_submit: bad query");
+        return IM_ERR_INVALID_ARG;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return IM_ERR_INVALID_ARG;
+        const uint64_t t = s->next_ticket++;
+        Request &r = s->reqs[t];
+        r.q = *q;
+        r.submitted = Clock::now();
+        r.footprint = footprint(s, *q);
+        s->queue.push_back(t);
+        *ticket = t;
+    }
+    s->cv_work.notify_one();
+    return IM_OK;
+}
+
+im_status im_server_poll(im_server *s, uint64_t ticket, int32_t *seeds, int32_t *num_seeds,
+                         int64_t *coverage, double *latency_ms) {
+    if (!s) return IM_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        set_error("im_server_poll: unknown ticket");
+        return IM_ERR_INVALID_ARG;
+    }
+    if (!it->second.done) return IM_ERR_BUSY;
+    return take_result(s, ticket, seeds, num_seeds, coverage, latency_ms, lk);
+}
+
+im_status im_server_wait(im_server *s, uint64_t ticket, double timeout_s, int32_t *seeds,
+                         int32_t *num_seeds, int64_t *coverage, double *latency_ms) {
+    if (!s) return IM_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        set_error("im_server_wait: unknown ticket");
+        return IM_ERR_INVALID_ARG;
+    }
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
+        auto jt = s->reqs.find(ticket);
+        return jt != s->reqs.end() && jt->second.done;
+    });
+    if (!ok) return IM_ERR_BUSY;
+    return take_result(s, ticket, seeds, num_seeds, coverage, latency_ms, lk);
+}
+
+im_status im_server_stats(im_server *s, int64_t *batches, int64_t *queries, int64_t *queued) {
+    if (!s) return IM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (batches) *batches = s->batches;
+    if (queries) *queries = s->batched_queries;
+    if (queued) *queued = (int64_t)s->queue.size();
+    return IM_OK;
+}
+
+}  // extern "C"

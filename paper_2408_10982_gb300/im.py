@@ -87,6 +87,12 @@ def lib():
                                        ctypes.c_int),
             "im_pool_reserve": ([vp, i64, i64], ctypes.c_int),
             "im_batch_create": ([pp], ctypes.c_int),
+            "im_server_create": ([vp, pp], ctypes.c_int),
+            "im_server_destroy": ([vp], ctypes.c_int),
+            "im_server_submit": ([vp, vp, vp], ctypes.c_int),
+            "im_server_poll": ([vp, ctypes.c_uint64, vp, vp, vp, vp], ctypes.c_int),
+            "im_server_wait": ([vp, ctypes.c_uint64, ctypes.c_double, vp, vp, vp, vp], ctypes.c_int),
+            "im_server_stats": ([vp, vp, vp, vp], ctypes.c_int),
             "im_batch_destroy": ([vp], ctypes.c_int),
             "im_solve_batch": ([vp, vp, i32, i32, vp, vp, vp, vp], ctypes.c_int),
             "im_solve": ([vp, ctypes.c_int, i32, ctypes.c_double, ctypes.c_double, u64, vp, vp,
@@ -293,6 +299,62 @@ def im_solve_batch(b, queries, kmax: int, stream=None):
         out.append((seeds[q * kmax:q * kmax + m].copy(), gains[q * kmax:q * kmax + m].copy(),
                     res[q].coverage, res[q].entries))
     return out
+
+
+class ServerOpts(ctypes.Structure):
+    """im_server_opts (see include/im.h)."""
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("mem_budget", ctypes.c_int64)]
+
+
+def im_server_create(workers: int = 2, max_batch: int = 256, mem_budget: int = 64 << 30):
+    h = ctypes.c_void_p()
+    o = ServerOpts(workers, max_batch, mem_budget)
+    _check(lib().im_server_create(ctypes.byref(o), ctypes.byref(h)), "im_server_create")
+    return h
+
+
+def im_server_destroy(s):
+    _check(lib().im_server_destroy(s), "im_server_destroy")
+
+
+def im_server_submit(s, graph, model: int, k: int, theta: int, seed: int) -> int:
+    q = Query(graph.value if hasattr(graph, "value") else graph, model, k, theta, seed)
+    t = ctypes.c_uint64()
+    _check(lib().im_server_submit(s, ctypes.byref(q), ctypes.byref(t)), "im_server_submit")
+    return t.value
+
+
+def im_server_wait(s, ticket: int, kmax: int, timeout_s: float = 600.0):
+    """(seeds, coverage, latency ms) of a request, blocking until it is done."""
+    seeds = np.zeros(max(kmax, 1), np.int32)
+    ns = ctypes.c_int32()
+    cov = ctypes.c_int64()
+    lat = ctypes.c_double()
+    _check(lib().im_server_wait(s, ticket, timeout_s, seeds.ctypes.data, ctypes.byref(ns),
+                                ctypes.byref(cov), ctypes.byref(lat)), "im_server_wait")
+    return seeds[: ns.value].copy(), cov.value, lat.value
+
+
+def im_server_poll(s, ticket: int, kmax: int):
+    """None while pending, else (seeds, coverage, latency ms)."""
+    seeds = np.zeros(max(kmax, 1), np.int32)
+    ns = ctypes.c_int32()
+    cov = ctypes.c_int64()
+    lat = ctypes.c_double()
+    st = lib().im_server_poll(s, ticket, seeds.ctypes.data, ctypes.byref(ns), ctypes.byref(cov),
+                              ctypes.byref(lat))
+    if st == IM_ERR_BUSY:
+        return None
+    _check(st, "im_server_poll")
+    return seeds[: ns.value].copy(), cov.value, lat.value
+
+
+def im_server_stats(s):
+    b, q, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().im_server_stats(s, ctypes.byref(b), ctypes.byref(q), ctypes.byref(w)),
+           "im_server_stats")
+    return b.value, q.value, w.value
 
 
 def im_pool_reserve(p, max_sets: int, max_entries: int):

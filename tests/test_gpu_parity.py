@@ -326,3 +326,38 @@ def test_solve_batch_matches_oracle_and_single_path(im):
                 assert cov == rc.coverage and entries == pool.members.size
     finally:
         im.im_batch_destroy(batch)
+
+
+def test_server_results_equal_alone(im):
+    """Continuous batching: requests submitted back to back land in shared
+    batches, and every result equals the oracle's (= the query alone)."""
+    import time
+    graphs = [inputs.rmat_graph(1 << 12, 1 << 16, 5, "ic0.1"),
+              inputs.rmat_graph(1 << 13, 1 << 17, 6, "lt")]
+    G = [im.Graph(g) for g in graphs]
+    srv = im.im_server_create(workers=2, max_batch=16, mem_budget=8 << 30)
+    rng = np.random.default_rng(3)
+    reqs = []
+    try:
+        for r in range(40):
+            gi = r % 2
+            k = int(rng.integers(1, 30))
+            th = int(rng.integers(100, 4000))
+            sd = int(rng.integers(0, 2**60))
+            t = im.im_server_submit(srv, G[gi].handle, im.IM_IC if gi == 0 else im.IM_LT, k, th, sd)
+            reqs.append((t, gi, k, th, sd))
+            if r % 7 == 0:
+                time.sleep(0.002)
+        for t, gi, k, th, sd in reqs:
+            seeds, cov, lat = im.im_server_wait(srv, t, 30)
+            g = graphs[gi]
+            pool = O.sample(O.IC if gi == 0 else O.LT, g, sd, 0, th)
+            rc = O.greedy(g.n, pool, O.invert(g.n, pool), k)
+            assert seeds.tolist() == rc.seeds.tolist() and cov == rc.coverage
+            assert lat > 0
+        batches, queries, queued = im.im_server_stats(srv)
+        assert queries == 40 and queued == 0 and batches < 40
+        with pytest.raises(im.ImError):
+            im.im_server_poll(srv, 10**9, 4)      # unknown (or already collected) ticket
+    finally:
+        im.im_server_destroy(srv)
