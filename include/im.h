@@ -183,10 +183,15 @@ im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
  *   IM_TUNE_LT_GROUP    lanes that run one LT walk: 8, 16 or 32 (default 8; a warp
  *                       then runs 32 / value walks at once).
  *   IM_TUNE_RG_CLUSTER  RandGreedi two-launch mode, bucket stage: 0 (default)
- *                       picks the smallest cluster of 1, 2, 4 or 8 blocks whose
- *                       shared memory holds a bucket's theta-bit bitmap; 1..8
- *                       asks for at least that many; -1 keeps the bitmaps in
- *                       global memory (one block per bucket). */
+ *                       keeps one 64-bit bucket mask per RRR set, so one pass
+ *                       over a streamed subset counts its gain for every
+ *                       bucket, and spreads each group of stream slots over
+ *                       the whole GPU (B <= 64; for B > 64 it picks a cluster
+ *                       as below); 1..8 keeps each bucket's theta-bit bitmap
+ *                       in the shared memory of a cluster of at least that
+ *                       many blocks (the smallest of 1, 2, 4, 8 that holds
+ *                       it); -1 keeps the bitmaps in global memory (one block
+ *                       per bucket). */
 typedef enum { IM_TUNE_LT_GROUP = 0, IM_TUNE_RG_CLUSTER = 1 } im_tune_knob;
 im_status im_tune_set(int32_t knob, int64_t value);
 im_status im_tune_get(int32_t knob, int64_t *value);

@@ -39,6 +39,9 @@ constexpr int kBatch = 256;                  // stream slots a consumer reads at
 constexpr int kUnroll = 8;                   // independent loads in flight per lane in scans
 constexpr int kSpec = 32;                    // largest speculative group of stream elements
 constexpr size_t kClusterSmemCap = 200 * 1024;  // bucket bitmap slice per block
+constexpr int kMaskG = 64;                   // largest group of stream slots (mask stage)
+constexpr int kMaskStrips = 16;              // entries per lane in one warp work item
+constexpr int kMaskItem = 32 * kMaskStrips;  // entries per warp work item
 
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v,
                                                             unsigned long long *sh) {
@@ -221,6 +224,10 @@ struct RGArgs {
     int32_t max_np;           // largest part: key[] and stamp[] are max_np each
     long long *stats;         // [P + B][6] diagnostics (see im_randgreedi_stats)
     int *status;
+    // bucket-mask stage (k_rg_stream_masks)
+    unsigned long long *mask; // [theta]: bit b set once bucket b covers the set
+    uint32_t *gbuf;           // [2][kMaskG][64] per-slot, per-bucket gains
+    GridBarrier *bar;
 };
 
 // Local greedy of part p (Alg. 4, one sender), run as the lazy greedy of
@@ -634,6 +641,204 @@ __global__ void __launch_bounds__(kRGThreads) k_rg_stream_cluster(RGArgs a, int6
     }
 }
 
+// Streaming buckets over per-set bucket masks (Alg. 5, run after the local
+// greedy has finished; B <= 64).  mask[i] holds one bit per bucket: bit b is
+// set once bucket b covers RRR set i.  A single pass over S(x) therefore
+// yields the marginal gain of x for every bucket at once -- the count of
+// entries whose bit b is clear -- instead of one pass per bucket.
+//
+// The stream is consumed in (j, p) slot order in speculative groups of up to
+// kMaskG slots.  Every warp of the grid takes work items of kMaskItem entries
+// of the group's subsets and adds its per-bucket counts to gbuf; after a grid
+// barrier every block replays the same sequential decision for each bucket
+// from those counts.  A count taken against the bucket as it stood at the
+// start of the group is exact until the bucket accepts something in the
+// group, and an upper bound after that (coverage only grows), so a later slot
+// below the threshold is still rejected exactly; a later slot at or above it
+// needs a fresh count, and the group is cut there for all buckets.  The
+// accepted subsets are then or-ed into the masks and the next group starts at
+// the cut.  Group sizes double after a group without a cut and halve after a
+// cut.
+__device__ __forceinline__ int mask_slot_of(const int64_t *s_off, int gn, int64_t c) {
+    int u = 0;
+    while (u + 1 < gn && s_off[u + 1] <= c) ++u;
+    return u;
+}
+
+__global__ void __launch_bounds__(kRGThreads) k_rg_stream_masks(RGArgs a) {
+    __shared__ int32_t s_x[kMaskG];
+    __shared__ int64_t s_beg[kMaskG], s_len[kMaskG];
+    __shared__ int64_t s_off[kMaskG + 1];            // work-item prefix over the group's slots
+    __shared__ unsigned long long s_acc[kMaskG];     // buckets accepting each slot
+    __shared__ int32_t s_n[64];
+    __shared__ int64_t s_cov[64];
+    __shared__ long long s_eval[64], s_scan[64];
+    __shared__ int s_cut;
+    const int lane = threadIdx.x & 31;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gwarp = gtid >> 5, nwarps = gstride >> 5;
+    const int64_t nslots = (int64_t)a.trunc * a.P;
+    const uint64_t t_begin = global_ns();
+    for (int64_t i = gtid; i < a.theta; i += gstride) a.mask[i] = 0ull;
+    for (int64_t i = gtid; i < 2 * kMaskG * 64; i += gstride) a.gbuf[i] = 0u;
+    if (threadIdx.x < 64) {
+        s_n[threadIdx.x] = 0;
+        s_cov[threadIdx.x] = 0;
+        s_eval[threadIdx.x] = 0;
+        s_scan[threadIdx.x] = 0;
+    }
+    if (!grid_sync(a.bar, gridDim.x, a.status)) return;
+    int64_t g0 = 0;
+    int G = 8, buf = 0;
+    while (g0 < nslots) {
+        const int gn = (int)(nslots - g0 < G ? nslots - g0 : G);
+        if (threadIdx.x < gn) {
+            const int64_t t = g0 + threadIdx.x;
+            const int32_t x = ld_acquire_u32(a.flags + t) == 1u ? __ldcg(a.elems + t) : -1;
+            s_x[threadIdx.x] = x;
+            const int64_t b = x >= 0 ? a.vtx_off[x] : 0;
+            s_beg[threadIdx.x] = b;
+            s_len[threadIdx.x] = x >= 0 ? a.vtx_off[x + 1] - b : 0;
+            s_acc[threadIdx.x] = 0ull;
+        }
+        if (threadIdx.x == 0) s_cut = gn;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t c = 0;
+            for (int u = 0; u < gn; ++u) {
+                s_off[u] = c;
+                c += (s_len[u] + kMaskItem - 1) / kMaskItem;
+            }
+            s_off[gn] = c;
+        }
+        __syncthreads();
+        uint32_t *gb = a.gbuf + (size_t)buf * kMaskG * 64;
+        // ---- counts of every slot of the group against the current masks
+        for (int64_t c = gwarp; c < s_off[gn]; c += nwarps) {
+            const int u = mask_slot_of(s_off, gn, c);
+            const int64_t e0 = (c - s_off[u]) * kMaskItem;
+            const int64_t len = s_len[u];
+            const int32_t *ids = a.set_ids + s_beg[u];
+            // 5-bit vertical counters, one bit-plane per 64-bit word
+            unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+#pragma unroll 4
+            for (int st = 0; st < kMaskStrips; ++st) {
+                const int64_t e = e0 + st * 32 + lane;
+                unsigned long long m = 0ull;
+                if (e < len) m = ~__ldcg(a.mask + __ldg(ids + e));
+                unsigned long long t = c0 & m;
+                c0 ^= m;
+                m = t;
+                t = c1 & m;
+                c1 ^= m;
+                m = t;
+                t = c2 & m;
+                c2 ^= m;
+                m = t;
+                t = c3 & m;
+                c3 ^= m;
+                m = t;
+                c4 |= m;
+            }
+            for (int b = 0; b < a.B; ++b) {
+                const uint32_t v = __popc(__ballot_sync(kFull, (c0 >> b) & 1ull)) +
+                                   (__popc(__ballot_sync(kFull, (c1 >> b) & 1ull)) << 1) +
+                                   (__popc(__ballot_sync(kFull, (c2 >> b) & 1ull)) << 2) +
+                                   (__popc(__ballot_sync(kFull, (c3 >> b) & 1ull)) << 3) +
+                                   (__popc(__ballot_sync(kFull, (c4 >> b) & 1ull)) << 4);
+                if (lane == (b & 31) && v) atomicAdd(gb + u * 64 + b, v);
+            }
+        }
+        if (!grid_sync(a.bar, gridDim.x, a.status)) return;
+        // ---- the sequential rule of every bucket, replayed in every block
+        const int b = threadIdx.x;
+        const bool own = b < a.B;
+        const int64_t T = own ? a.thr[b] : 0;
+        if (own) {
+            int32_t nb = s_n[b];
+            bool took = false;
+            for (int u = 0; u < gn && nb < a.k; ++u) {
+                if (s_x[u] < 0) continue;
+                if ((int64_t)__ldcg(gb + u * 64 + b) >= T) {
+                    if (took) {
+                        atomicMin(&s_cut, u);
+                        break;
+                    }
+                    took = true;
+                    ++nb;
+                }
+            }
+        }
+        __syncthreads();
+        const int cut = s_cut;
+        if (own) {
+            int32_t nb = s_n[b];
+            int64_t cov = s_cov[b];
+            for (int u = 0; u < cut && nb < a.k; ++u) {
+                if (s_x[u] < 0) continue;
+                const int64_t g = (int64_t)__ldcg(gb + u * 64 + b);
+                ++s_eval[b];
+                s_scan[b] += s_len[u];
+                if (g >= T) {
+                    atomicOr(&s_acc[u], 1ull << b);
+                    if (blockIdx.x == 0) {
+                        a.bucket_seeds[(int64_t)b * a.k + nb] = s_x[u];
+                        a.bucket_gains[(int64_t)b * a.k + nb] = g;
+                    }
+                    ++nb;
+                    cov += g;
+                }
+            }
+            s_n[b] = nb;
+            s_cov[b] = cov;
+        }
+        __syncthreads();
+        // ---- or the accepted subsets into the masks; clear the other buffer
+        if (threadIdx.x == 0) {
+            int64_t c = 0;
+            for (int u = 0; u < cut; ++u) {
+                s_off[u] = c;
+                if (s_acc[u]) c += (s_len[u] + kMaskItem - 1) / kMaskItem;
+            }
+            s_off[cut] = c;
+        }
+        __syncthreads();
+        for (int64_t c = gwarp; c < s_off[cut]; c += nwarps) {
+            int u = 0;
+            while (u + 1 < cut && (s_off[u + 1] <= c || !s_acc[u])) ++u;
+            const unsigned long long acc = s_acc[u];
+            const int64_t e0 = (c - s_off[u]) * kMaskItem;
+            const int64_t len = s_len[u];
+            const int32_t *ids = a.set_ids + s_beg[u];
+            for (int st = 0; st < kMaskStrips; ++st) {
+                const int64_t e = e0 + st * 32 + lane;
+                if (e < len) atomicOr(a.mask + __ldg(ids + e), acc);
+            }
+        }
+        uint32_t *other = a.gbuf + (size_t)(buf ^ 1) * kMaskG * 64;
+        for (int64_t i = gtid; i < kMaskG * 64; i += gstride) other[i] = 0u;
+        if (!grid_sync(a.bar, gridDim.x, a.status)) return;
+        g0 += cut;
+        buf ^= 1;
+        G = cut < gn ? (G > 1 ? G / 2 : 1) : (G < kMaskG ? G * 2 : kMaskG);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < a.B) {
+        const int b = threadIdx.x;
+        a.bucket_n[b] = s_n[b];
+        a.bucket_cov[b] = s_cov[b];
+        if (a.stats) {
+            long long *st = a.stats + 6 * ((int64_t)a.P + b);
+            st[0] = (long long)t_begin;
+            st[1] = (long long)global_ns();
+            st[2] = s_eval[b];
+            st[3] = s_n[b];
+            st[4] = s_scan[b];
+            st[5] = 0;
+        }
+    }
+}
+
 // Alg. 4's final compare: best bucket (ties: smallest b) against the best
 // local solution (ties: smallest p); the bucket wins ties.
 __global__ void k_rg_final(RGArgs a, int32_t *seeds, int64_t *gains, int32_t *nseeds,
@@ -834,6 +1039,11 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     const size_t o_flags = take((size_t)trunc * P * 4);
     const size_t o_elems = take((size_t)trunc * P * 4);
     const size_t o_l = take(64);
+    // bucket-mask stage (two-launch mode, automatic layout, B <= 64)
+    const bool use_masks = o->fused == 0 && tune_value(IM_TUNE_RG_CLUSTER) == 0 && B <= 64;
+    const size_t o_mask = use_masks ? take((size_t)std::max<int64_t>(theta, 1) * 8) : 0;
+    const size_t o_gbuf = use_masks ? take((size_t)2 * kMaskG * 64 * 4) : 0;
+    const size_t o_bar = use_masks ? take(sizeof(GridBarrier)) : 0;
     void *base = nullptr;
     s = pool_scratch(p, off, &base);
     if (s != IM_OK) return s;
@@ -885,6 +1095,10 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     a.status = d_status;
     a.max_np = std::max(max_np, 1);
     a.stats = p->rg_stats;
+    a.mask = use_masks ? (unsigned long long *)(Bs + o_mask) : nullptr;
+    a.gbuf = use_masks ? (uint32_t *)(Bs + o_gbuf) : nullptr;
+    a.bar = use_masks ? (GridBarrier *)(Bs + o_bar) : nullptr;
+    if (use_masks) IM_CUDA(cudaMemsetAsync(Bs + o_bar, 0, sizeof(GridBarrier), st));
 
     IM_CUDA(cudaFuncSetAttribute(k_randgreedi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)prod_smem));
@@ -913,8 +1127,20 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
             k_randgreedi<<<a.nprod, kRGThreads, prod_smem, st>>>(a);
         }
         IM_CUDA(cudaGetLastError());
-        // buckets: shared-memory bitmaps split over a cluster when theta fits
         const int64_t want = tune_value(IM_TUNE_RG_CLUSTER);   // 0 auto, -1 off, 1..8
+        if (use_masks) {
+            // buckets: one pass over each streamed subset serves all buckets
+            int per = 0;
+            IM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rg_stream_masks,
+                                                                  kRGThreads, 0));
+            if (per < 1) return IM_ERR_UNSUPPORTED;
+            const int grid = std::min(per, 2) * num_sms();
+            void *args[] = {&a};
+            KernelTimer kt(st, "randgreedi_stream");
+            IM_CUDA(cudaLaunchCooperativeKernel((const void *)k_rg_stream_masks, dim3(grid),
+                                                dim3(kRGThreads), args, 0, st));
+        }
+        // buckets: shared-memory bitmaps split over a cluster when theta fits
         int CS = want > 0 ? (int)want : 1;
         int64_t R = 0;
         size_t csmem = 0;
@@ -924,7 +1150,9 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
             if (csmem <= kClusterSmemCap) break;
         }
         if (want < 0) CS = 16;   // global-memory bitmaps requested
-        if (CS <= 8) {
+        if (use_masks) {
+            // done above
+        } else if (CS <= 8) {
             unsigned *counter = (unsigned *)(Bs + o_l) + 2;
             IM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
             IM_CUDA(cudaFuncSetAttribute(k_rg_stream_cluster,
