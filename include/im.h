@@ -180,8 +180,12 @@ im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out
 im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
 
 /* ---- tuning knobs (process-wide; results never depend on them) ---------------
- *   IM_TUNE_LT_GROUP    lanes that run one LT walk: 8, 16 or 32 (default 8; a warp
- *                       then runs 32 / value walks at once).
+ *   IM_TUNE_LT_GROUP    lanes that run one LT walk: 1 (default: one walk per
+ *                       thread, an exact cut-point table picks the in-edge in
+ *                       O(1) expected loads, revisits are tested through a
+ *                       per-walk Bloom filter), or 8, 16, 32 (a warp runs
+ *                       32 / value walks in lockstep over a fanout-32 search
+ *                       tree of the running sums).
  *   IM_TUNE_RG_CLUSTER  RandGreedi two-launch mode, bucket stage: 0 (default)
  *                       keeps one 64-bit bucket mask per RRR set, so one pass
  *                       over a streamed subset counts its gain for every

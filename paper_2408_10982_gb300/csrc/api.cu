@@ -97,7 +97,7 @@ KernelTimer::~KernelTimer() {
 
 namespace {
 std::mutex g_tune_mu;
-int64_t g_tune[2] = {8, 0};   // IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER
+int64_t g_tune[2] = {1, 0};   // IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER
 }  // namespace
 
 int64_t tune_value(int32_t knob) {
@@ -311,6 +311,7 @@ im_status im_graph_destroy(im_graph *g) {
     cudaFree(g->lt_vrec);
     cudaFree(g->lt_leaf);
     cudaFree(g->lt_tree);
+    cudaFree(g->lt_guide);
     delete g;
     return IM_OK;
 }
@@ -546,7 +547,7 @@ im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes) {
 }
 
 im_status im_tune_set(int32_t knob, int64_t value) {
-    const bool ok = (knob == IM_TUNE_LT_GROUP && (value == 8 || value == 16 || value == 32)) ||
+    const bool ok = (knob == IM_TUNE_LT_GROUP && (value == 1 || value == 8 || value == 16 || value == 32)) ||
                     (knob == IM_TUNE_RG_CLUSTER &&
                      (value == -1 || value == 0 || value == 1 || value == 2 || value == 4 ||
                       value == 8));

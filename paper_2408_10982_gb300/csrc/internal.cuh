@@ -161,6 +161,7 @@ struct QueryView {
     const uint4 *lt_vrec;
     const unsigned long long *lt_leaf;
     const unsigned long long *lt_tree;
+    const uint4 *lt_guide;
     uint64_t seed;
     uint32_t n;
     uint32_t first;      // sample id of the query's first sample
@@ -180,6 +181,7 @@ struct im_graph {
     uint4 *lt_vrec;                  // [n] {edge offset, in-degree, tree offset, 0}
     unsigned long long *lt_leaf;     // [m]
     unsigned long long *lt_tree;     // [sum over vertices of the upper-level sizes]
+    uint4 *lt_guide;                 // [m] inverse-CDF cut points (see k_lt_guide)
     int32_t lt_valid;
     int64_t max_indeg;
 };

@@ -435,6 +435,197 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
     if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
 }
 
+// LT, one walk per thread.  A step is one Philox draw, the vertex record and
+// one guide entry (see k_lt_guide): two dependent loads for any in-degree,
+// with a binary search over the running sums only when the draw lies past
+// the guide's edge.  The revisit test goes through a 1024-bit Bloom filter of
+// the walk in shared memory (two hashes); only a hit is checked exactly, by
+// the whole warp scanning that walk's path.  Finished walks are copied to the
+// stage by the whole warp as well, after one warp-wide reservation.
+constexpr int kLT1Threads = 256;
+constexpr int kBloomWords = 32;              // 1024 bits per walk
+constexpr int64_t kQueueCapLT1 = 512;
+
+__device__ __forceinline__ uint32_t bloom_h1(uint32_t u) { return (u * 0x9E3779B1u) >> 22; }
+__device__ __forceinline__ uint32_t bloom_h2(uint32_t u) {
+    return ((u ^ (u >> 16)) * 0x85EBCA6Bu) >> 22;
+}
+
+// bl points at this thread's column: word w of its filter is bl[w * kLT1Threads]
+// (a warp touching any words hits 32 distinct banks)
+__device__ __forceinline__ void bloom_add(uint32_t *bl, uint32_t u) {
+    const uint32_t h1 = bloom_h1(u), h2 = bloom_h2(u);
+    bl[(h1 >> 5) * kLT1Threads] |= 1u << (h1 & 31);
+    bl[(h2 >> 5) * kLT1Threads] |= 1u << (h2 & 31);
+}
+
+__device__ __forceinline__ bool bloom_has(const uint32_t *bl, uint32_t u) {
+    const uint32_t h1 = bloom_h1(u), h2 = bloom_h2(u);
+    return ((bl[(h1 >> 5) * kLT1Threads] >> (h1 & 31)) & (bl[(h2 >> 5) * kLT1Threads] >> (h2 & 31)) &
+            1u) != 0;
+}
+
+__global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
+    extern __shared__ uint32_t bloom[];          // [kBloomWords][kLT1Threads]
+    const int lane = threadIdx.x & 31;
+    uint32_t *bl = bloom + threadIdx.x;
+    const int64_t slot0 = (int64_t)blockIdx.x * kLT1Threads + (threadIdx.x & ~31);
+    int32_t *q = a.queues + (slot0 + lane) * a.qcap;
+    bool active = false, exhausted = false;
+    int64_t j = 0;
+    uint32_t s = 0, cur = 0, k0 = 0, k1 = 0;
+    const uint4 *vrec = nullptr, *guide = nullptr;
+    const unsigned long long *leaf = nullptr;
+    int32_t len = 0;
+    unsigned long long sexam = 0, exam = 0, abytes = 0;
+    uint32_t sbytes = 0;
+    for (;;) {
+        // ---- lanes without a walk take the next samples (one atomic per warp)
+        const bool want = !active && !exhausted;
+        const unsigned need = __ballot_sync(kFull, want);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(need));
+            base = __shfl_sync(kFull, base, leader);
+            if (want) {
+                const unsigned long long jw = base + __popc(need & ((1u << lane) - 1u));
+                if (jw < (unsigned long long)a.count) {
+                    j = a.list ? a.list[jw] : (int64_t)jw;
+                    const int qi = find_query(a, j);
+                    const QueryView &V = a.qv[qi];
+                    vrec = V.lt_vrec;
+                    guide = V.lt_guide;
+                    leaf = V.lt_leaf;
+                    k0 = seed_lo(V.seed);
+                    k1 = seed_hi(V.seed);
+                    s = V.first + (uint32_t)(j - __ldg(a.qstart + qi));
+                    cur = rrr_root(V.seed, s, V.n);
+                    q[0] = (int32_t)cur;
+#pragma unroll
+                    for (int w = 0; w < kBloomWords; ++w) bl[w * kLT1Threads] = 0u;
+                    bloom_add(bl, cur);
+                    len = 1;
+                    sexam = 0;
+                    sbytes = 8;
+                    active = true;
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(kFull, active)) break;
+
+        // ---- one step of every active walk
+        bool picked = false;
+        uint32_t u = 0;
+        if (active) {
+            const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
+            const uint4 vr = __ldg(vrec + cur);
+            const uint32_t d = vr.y;
+            int64_t e = -1;
+            if (d > 0) {
+                const uint4 gv = __ldg(guide + vr.x + __umulhi(x, d));
+                const unsigned long long cum = ((unsigned long long)gv.y << 32) | gv.x;
+                if ((unsigned long long)x < cum) {
+                    e = gv.w;
+                    u = gv.z;
+                } else {
+                    uint32_t lo = gv.w + 1, hi = d;  // first edge past the guide's with x < sum
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if ((unsigned long long)x < (__ldg(leaf + vr.x + mid) >> 31)) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    if (lo < d) {
+                        e = lo;
+                        u = (uint32_t)(__ldg(leaf + vr.x + lo) & 0x7fffffffull);
+                    }
+                }
+            }
+            picked = e >= 0;
+            sexam += picked ? (unsigned long long)(e + 1) : (unsigned long long)d;
+            // offsets, binary search of d running sums, source, member write
+            sbytes += 16u + (d > 0 ? 8u * (uint32_t)(32 - __clz(d)) : 0u) + (picked ? 4u : 0u) + 4u;
+        }
+        // ---- revisit test: Bloom filter, then an exact scan of the flagged walks
+        unsigned hits = __ballot_sync(kFull, picked && bloom_has(bl, u));
+        bool seen = false;
+        if (hits) {
+            __syncwarp();
+            do {
+                const int l = __ffs(hits) - 1;
+                hits &= hits - 1;
+                const int32_t ul = __shfl_sync(kFull, (int32_t)u, l);
+                const int32_t ll = __shfl_sync(kFull, len, l);
+                const int32_t *ql = a.queues + (slot0 + l) * a.qcap;
+                bool f = false;
+                for (int32_t i = lane; i < ll; i += 32) f |= __ldcg(ql + i) == ul;
+                const bool any = __any_sync(kFull, f);
+                if (lane == l) seen = any;
+            } while (hits);
+        }
+        bool ovf = false;
+        if (picked && !seen) {
+            if (len < a.qcap) {
+                q[len] = (int32_t)u;
+                bloom_add(bl, u);
+                ++len;
+                cur = u;
+            } else {
+                ovf = true;
+            }
+        }
+        const bool ending = active && !(picked && !seen && !ovf);
+        if (ending && ovf) {                         // longer than the queue: second pass
+            a.sizes[j] = -1;
+            a.stage_off[j] = 0;
+            a.ovf_list[atomicAdd(a.ovf_count, 1ull)] = j;
+        }
+        // ---- finished walks go to the stage
+        const bool emit = ending && !ovf;
+        unsigned em = __ballot_sync(kFull, emit);
+        if (em) {
+            const int32_t my = emit ? len : 0;
+            const int32_t incl = warp_incl_scan<int32_t>(my, lane);
+            const int32_t tot = __shfl_sync(kFull, incl, 31);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.stage_cursor, (unsigned long long)tot);
+            base = __shfl_sync(kFull, base, 0);
+            const bool fits = (int64_t)base + tot <= a.stage_cap;
+            if (emit) {
+                if (fits) {
+                    a.stage_off[j] = (int64_t)base + incl - my;
+                    a.sizes[j] = len;
+                    exam += sexam;
+                    abytes += sbytes;
+                } else {
+                    raise_status(a.status, kDevStageOverflow);
+                    a.sizes[j] = 0;
+                    a.stage_off[j] = 0;
+                }
+            }
+            if (fits) {
+                __syncwarp();
+                do {
+                    const int l = __ffs(em) - 1;
+                    em &= em - 1;
+                    const int32_t ll = __shfl_sync(kFull, len, l);
+                    const int64_t pl = (int64_t)base + __shfl_sync(kFull, incl - my, l);
+                    const int32_t *ql = a.queues + (slot0 + l) * a.qcap;
+                    for (int32_t i = lane; i < ll; i += 32) a.stage[pl + i] = __ldcg(ql + i);
+                } while (em);
+            }
+        }
+        if (ending) active = false;
+        __syncwarp();
+    }
+    exam = warp_sum<unsigned long long>(exam);
+    abytes = warp_sum<unsigned long long>(abytes);
+    if (lane == 0 && exam) atomicAdd(a.examined, exam);
+    if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
+}
+
 // LT search index.  vrec[v] = {eb, d, tree offset, number of upper levels L}.
 // For vertex v with in-edges [eb, eb + d):
 //   leaf[e] = (sum of w over v's in-edges up to and including e) << 31 | src(e)
@@ -490,6 +681,40 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
             }
             lvl += sz;
         }
+    }
+}
+
+// Cut points of the inverse-CDF pick, exact for any weights.  A draw x of
+// vertex v (in-edges [eb, eb + d)) falls in bucket b = floor(x d / 2^32); the
+// smallest draw of bucket b is lo_b = ceil(b 2^32 / d).  guide[eb + b]
+// describes the first in-edge e whose running sum exceeds lo_b, or the last
+// in-edge when none does: {running sum low word, high word, source, e}.
+// Every edge before e has a running sum <= lo_b <= x, so x picks e exactly
+// when x < running sum(e); otherwise the pick lies after e (or there is none).
+__global__ void k_lt_guide(const int64_t *in_off, const unsigned long long *leaf, int64_t n,
+                           int64_t m, uint4 *guide) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n - 1;                  // vertex owning position t
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (in_off[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t eb = in_off[lo], d = in_off[lo + 1] - eb, b = t - eb;
+        const unsigned long long lob =
+            (((unsigned long long)b << 32) + (unsigned long long)d - 1ull) / (unsigned long long)d;
+        int64_t l2 = 0, h2 = d;                      // first e with lo_b < running sum(e)
+        while (l2 < h2) {
+            const int64_t mid = (l2 + h2) >> 1;
+            if (lob < (leaf[eb + mid] >> 31)) h2 = mid;
+            else l2 = mid + 1;
+        }
+        const int64_t e = l2 < d ? l2 : d - 1;
+        const unsigned long long r = leaf[eb + e];
+        const unsigned long long cum = r >> 31;
+        guide[t] = make_uint4((uint32_t)cum, (uint32_t)(cum >> 32), (uint32_t)(r & 0x7fffffffull),
+                              (uint32_t)e);
     }
 }
 
@@ -734,6 +959,12 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
                                                   g->lt_tree, g->lt_vrec, n, d_invalid);
     }
     IM_CUDA(cudaGetLastError());
+    IM_CUDA(cudaMalloc(&g->lt_guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
+    if (m > 0) {
+        KernelTimer kt(st, "lt_index");
+        k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->lt_leaf, n, m, g->lt_guide);
+    }
+    IM_CUDA(cudaGetLastError());
     int invalid = 0;
     IM_CUDA(cudaMemcpyAsync(&invalid, d_invalid, sizeof(int), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaFreeAsync(sizes, st));
@@ -752,6 +983,7 @@ QueryView query_view(const im_graph *g, uint64_t seed, uint64_t first) {
     v.lt_vrec = g->lt_vrec;
     v.lt_leaf = g->lt_leaf;
     v.lt_tree = g->lt_tree;
+    v.lt_guide = g->lt_guide;
     v.seed = seed;
     v.n = (uint32_t)g->n;
     v.first = (uint32_t)first;
@@ -774,26 +1006,32 @@ im_status run_sampling(const SamplingJob &job, const std::function<im_status(siz
 
     // launch shape: persistent, occupancy-sized
     const int G = model == IM_LT ? (int)tune_value(IM_TUNE_LT_GROUP) : 32;
+    const bool lt1 = model == IM_LT && G == 1;      // one walk per thread
     const void *kern = model == IM_LT
-                           ? (G == 8    ? (const void *)k_sample_lt<8>
+                           ? (G == 1    ? (const void *)k_sample_lt1
+                              : G == 8  ? (const void *)k_sample_lt<8>
                               : G == 16 ? (const void *)k_sample_lt<16>
                                         : (const void *)k_sample_lt<32>)
                        : smem_vis ? (const void *)k_sample_ic<true>
                                   : (const void *)k_sample_ic<false>;
-    const size_t dyn_smem = smem_vis ? (size_t)kWarps * vis_words * 4 : 0;
-    if (smem_vis && dyn_smem > 48 * 1024)
+    const int threads = lt1 ? kLT1Threads : kSampleThreads;
+    const size_t dyn_smem = smem_vis ? (size_t)kWarps * vis_words * 4
+                            : lt1    ? (size_t)kBloomWords * kLT1Threads * 4
+                                     : 0;
+    if (dyn_smem > 48 * 1024)
         IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)dyn_smem));
-    int blocks = blocks_for(kern, kSampleThreads, dyn_smem);
+    int blocks = blocks_for(kern, threads, dyn_smem);
     // global visited bitmaps are n bits per warp: keep them within ~2 GB
     if (model == IM_IC && !smem_vis) {
         int64_t cap_blocks = std::max<int64_t>(
             num_sms(), (int64_t)(2ll << 30) / ((int64_t)kWarps * vis_words * 4));
         blocks = (int)std::min<int64_t>(blocks, cap_blocks);
     }
-    const int64_t warps = (int64_t)blocks * kWarps;
+    const int64_t warps = (int64_t)blocks * (threads / 32);
     const int64_t slots = warps * (32 / G);           // one queue per walk in flight
-    const int64_t qcap = std::min<int64_t>(n, model == IM_LT ? kQueueCapLT : kQueueCapIC);
+    const int64_t qcap = std::min<int64_t>(
+        n, lt1 ? kQueueCapLT1 : model == IM_LT ? kQueueCapLT : kQueueCapIC);
 
     // scratch layout
     size_t off = 0;
@@ -852,7 +1090,8 @@ im_status run_sampling(const SamplingJob &job, const std::function<im_status(siz
     auto launch = [&](int nblocks, int group) {
         KernelTimer kt(st, model == IM_LT ? "sample_lt" : "sample_ic");
         if (model == IM_LT) {
-            if (group == 8) k_sample_lt<8><<<nblocks, kSampleThreads, 0, st>>>(a);
+            if (group == 1) k_sample_lt1<<<nblocks, kLT1Threads, dyn_smem, st>>>(a);
+            else if (group == 8) k_sample_lt<8><<<nblocks, kSampleThreads, 0, st>>>(a);
             else if (group == 16) k_sample_lt<16><<<nblocks, kSampleThreads, 0, st>>>(a);
             else k_sample_lt<32><<<nblocks, kSampleThreads, 0, st>>>(a);
         } else if (smem_vis) {

@@ -237,7 +237,7 @@ def test_randgreedi_ic_small(im, fused):
     _rg_compare(im, g, im.IM_IC, 16384, 16, 148, (1, 4), 0.077, fused)
 
 
-@pytest.mark.parametrize("group", [8, 16, 32])
+@pytest.mark.parametrize("group", [1, 8, 16, 32])
 def test_lt_group_sizes_identical(im, group):
     """Lanes per LT walk is a tuning knob: every setting gives the same pool."""
     g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
