@@ -6,8 +6,8 @@ One step = the whole hot path over one batch of synthetic input:
   -> covering-subset index (histogram, scan, scatter)
   -> plain greedy max-k-cover                        (im_max_k_cover, greedy)
   -> RandGreedi: 148 vertex parts, lazy local greedy, then the streaming
-     threshold buckets over the first ceil(k/4) local seeds of every part, each
-     bucket's bitmap in the shared memory of a thread-block cluster
+     threshold buckets over the first ceil(k/4) local seeds of every part,
+     counted for all buckets at once over per-set bucket masks
                                                      (im_max_k_cover, RandGreedi)
 Workload: R-MAT scale 20 (1,048,576 vertices, 16,777,216 edges, a/b/c/d =
 0.57/0.19/0.19/0.05, seed 42), LT weights 1/in-degree quantised to uint32,
@@ -18,6 +18,12 @@ LT cumulative-weight search decides over, identical to the oracle's count),
 with the graph resident in HBM.  `e2e` is the same metric through the C ABI
 from pinned host arrays: graph upload, LT index build, sampling, both covers
 and the read-back of seeds every step.
+
+Beside the step, the line carries three sections measured after it:
+`batched` (256 queries of the batched mix in one im_solve_batch call against
+the one-query path), `served` (Poisson arrivals at 200/s through im_server
+against the one-query path as a FIFO server: q/s, p50/p99 latency) and `ic`
+(IC sampling on the LiveJournal-shaped graph).
 
 --impl reference runs the CPU oracle (oracle/, the plain definition) on a
 bounded sample of the same workload on rank 0.
@@ -70,6 +76,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--rg-fused", type=int, default=0,
                     help="RandGreedi as one cooperative launch (1) or two launches (0)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the IC, batched and served sections")
+    ap.add_argument("--served-orkut", action="store_true",
+                    help="served trace with 5%% Orkut-shaped queries (generates a 234M-edge graph)")
     return ap.parse_args()
 
 
@@ -301,10 +311,14 @@ def run_ours(args):
         line["bit_exact"], line["cpu_baseline"] = cpu_baseline_and_check(g, pool, first)
     if not args.no_e2e:
         line["e2e"] = e2e(args, g, im, torch, dev, stream, first, dist)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     pool.close()
     G.close()
+    if not args.no_extras:
+        line["batched"] = bench_batched(im, torch)
+        line["served"] = bench_served(im, torch, args.served_orkut)
+        line["ic"] = bench_ic(im, torch)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
@@ -366,6 +380,179 @@ def e2e(args, g, im, torch, dev, stream, first, dist):
     d2h = 2 * (4 * K + 8 * K + 4 + 8)
     return {"value": world * examined / dt, "unit": "edges/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(1000 * dt, 3), "steps": steps}
+
+
+# ---------------------------------------------------------------------------
+# IC sampling, batched queries, served queries
+# ---------------------------------------------------------------------------
+
+class OneQuery:
+    """The plain one-query-at-a-time GPU path: im_sample_rrr into a reused pool
+    of the query's graph, then im_max_k_cover (plain greedy), seeds read back."""
+
+    def __init__(self, im, G):
+        self.im, self.G = im, G
+        self.pools = {}
+        self.caps = {}
+
+    def solve(self, name, model, k, theta, seed):
+        im = self.im
+        p = self.pools.get(name)
+        if p is None:
+            self.caps[name] = (max(theta, 1), max(theta, 1) * 32)
+            p = self.pools[name] = im.Pool(self.G[name], *self.caps[name])
+        while True:
+            sets, ents = self.caps[name]
+            if theta > sets or theta * 32 > ents:
+                self.caps[name] = (max(sets, theta), max(ents, theta * 32))
+                im.im_pool_reserve(p.handle, *self.caps[name])
+            p.reset()
+            try:
+                p.sample(model, seed, 0, theta)
+                break
+            except im.ImError as e:
+                if e.status != im.IM_ERR_CAPACITY:
+                    raise
+                sets, ents = self.caps[name]
+                self.caps[name] = (sets, ents * 4)
+                im.im_pool_reserve(p.handle, *self.caps[name])
+        c = p.cover(k)
+        return c.seeds, c.coverage
+
+    def close(self):
+        for p in self.pools.values():
+            p.close()
+
+
+def _batched_graphs(im):
+    graphs = {f"rmat{s}": inputs.batched_graph(s, SEED) for s in inputs.BATCH_SCALES}
+    return graphs, {name: im.Graph(g) for name, g in graphs.items()}
+
+
+def bench_batched(im, torch):
+    """256 queries of the batched mix: one im_solve_batch call versus the
+    one-query path run back to back; results compared query by query."""
+    specs = inputs.batched_queries(256, SEED)
+    graphs, G = _batched_graphs(im)
+    qlist = [(G[q.graph].handle, q.model, q.k, q.theta, q.seed) for q in specs]
+    batch = im.im_batch_create()
+    im.im_solve_batch(batch, qlist, 100)                 # warm-up (sizes the arenas)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = im.im_solve_batch(batch, qlist, 100)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    im.im_batch_destroy(batch)
+    one = OneQuery(im, G)
+    for q in specs[:8]:                                   # warm-up
+        one.solve(q.graph, q.model, q.k, q.theta, q.seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [one.solve(q.graph, q.model, q.k, q.theta, q.seed) for q in specs]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    one.close()
+    same = all(a[0].tolist() == b[0].tolist() and a[2] == b[1] for a, b in zip(out, plain))
+    entries = sum(o[3] for o in out)
+    for g in G.values():
+        g.close()
+    return {"workload": "256 queries: R-MAT scales 12..18 (edge factor 16), IC (weighted cascade "
+                        "1/in-degree) or LT (1/in-degree), k in [5,100], theta in [2^14,2^20]",
+            "queries": len(specs), "sets": sum(q.theta for q in specs), "entries": entries,
+            "q_per_s": round(len(specs) / t_batch, 2), "ms": round(1000 * t_batch, 2),
+            "plain_q_per_s": round(len(specs) / t_plain, 2), "plain_ms": round(1000 * t_plain, 2),
+            "speedup_vs_plain": round(t_plain / t_batch, 3), "bit_exact_vs_plain": bool(same)}
+
+
+def bench_served(im, torch, orkut: bool):
+    """Poisson arrivals (mean 200/s) replayed in real time into im_server
+    (continuous batching), versus the one-query path as a FIFO server: each
+    query's service time is measured back to back and the trace is replayed
+    through a single queue (done_i = max(arrival_i, done_{i-1}) + service_i)."""
+    nq = 512
+    specs = inputs.served_trace(nq, SEED, orkut_frac=0.05 if orkut else 0.0)
+    graphs, G = _batched_graphs(im)
+    if any(q.graph == "orkut" for q in specs):
+        G["orkut"] = im.Graph(inputs.graph_orkut_like(SEED))
+    srv = im.im_server_create(workers=2, max_batch=64, mem_budget=96 << 30)
+    warm = [im.im_server_submit(srv, G[q.graph].handle, q.model, q.k, q.theta, q.seed)
+            for q in specs[:16]]
+    for t in warm:
+        im.im_server_wait(srv, t, 100, 600)
+    b0, q0, _ = im.im_server_stats(srv)
+    tickets = []
+    t0 = time.perf_counter()
+    for q in specs:
+        delay = q.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(im.im_server_submit(srv, G[q.graph].handle, q.model, q.k, q.theta, q.seed))
+    res = [im.im_server_wait(srv, t, 100, 600) for t in tickets]
+    t_all = time.perf_counter() - t0
+    b1, q1, _ = im.im_server_stats(srv)
+    im.im_server_destroy(srv)
+    lat = np.array([r[2] for r in res])
+    one = OneQuery(im, G)
+    for q in specs[:8]:
+        one.solve(q.graph, q.model, q.k, q.theta, q.seed)
+    torch.cuda.synchronize()
+    service, plain = [], []
+    for q in specs:
+        t1 = time.perf_counter()
+        plain.append(one.solve(q.graph, q.model, q.k, q.theta, q.seed))
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t1)
+    one.close()
+    done, plat = 0.0, []
+    for q, sv in zip(specs, service):
+        done = max(q.arrival_s, done) + sv
+        plat.append(1000 * (done - q.arrival_s))
+    plat = np.array(plat)
+    same = all(a[0].tolist() == b[0].tolist() and a[1] == b[1] for a, b in zip(res, plain))
+    for g in G.values():
+        g.close()
+    return {"workload": f"{nq} Poisson arrivals at 200/s from the batched mix"
+                        + (", 5% Orkut-shaped (IC p=0.01, theta in [2^6,2^10])" if orkut else ""),
+            "queries": nq, "span_s": round(specs[-1].arrival_s, 3),
+            "q_per_s": round(nq / t_all, 2), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+            "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "batches": int(b1 - b0), "mean_batch": round((q1 - q0) / max(b1 - b0, 1), 2),
+            "plain_q_per_s": round(nq / max(done, specs[-1].arrival_s), 2),
+            "plain_p50_ms": round(float(np.percentile(plat, 50)), 2),
+            "plain_p99_ms": round(float(np.percentile(plat, 99)), 2),
+            "plain_busy_s": round(float(sum(service)), 3),
+            "bit_exact_vs_plain": bool(same)}
+
+
+def bench_ic(im, torch):
+    """IC sampling on the LiveJournal-shaped graph (trivalency), 8,192 sets."""
+    g = inputs.graph_livejournal_like(SEED)
+    G = im.Graph(g)
+    theta = 8192
+    p = im.Pool(G, theta, theta * 600_000)
+    p.sample(im.IM_IC, SEED, 0, 1024)                  # warm-up
+    p.reset()
+    im.im_profile_reset()
+    im.im_profile_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p.sample(im.IM_IC, SEED, 1 << 20, theta)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    im.im_profile_enable(False)
+    prof = im.im_profile_read()
+    _, total, examined = p.info()
+    sbytes = p.sample_bytes()
+    k_ms = prof.get("sample_ic", (1, 0.0))[1]
+    hbm, _ = measured_peaks()
+    p.close()
+    G.close()
+    return {"workload": "LiveJournal-shaped R-MAT (4,847,571 vertices, 69,000,000 edges), IC "
+                        "trivalency, 8,192 RRR sets", "edges_per_s": examined / dt,
+            "entries": total, "ms": round(1000 * dt, 3), "kernel_ms": round(k_ms, 3),
+            "kernel_gbs": round(sbytes / (k_ms / 1000) / 1e9, 1) if k_ms else None,
+            "kernel_frac": round(sbytes / (k_ms / 1000) / 1e9 / hbm, 4) if k_ms else None,
+            "phase_ms": {k: round(v[1], 3) for k, v in sorted(prof.items())}}
 
 
 def main():

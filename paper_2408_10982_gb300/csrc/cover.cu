@@ -228,6 +228,8 @@ struct RGArgs {
     unsigned long long *mask; // [theta]: bit b set once bucket b covers the set
     uint32_t *gbuf;           // [2][kMaskG][64] per-slot, per-bucket gains
     GridBarrier *bar;
+    int32_t *slot_x;          // [trunc * P] element of each stream slot, -1 if none
+    int64_t *slot_beg, *slot_len;   // its covering subset in set_ids
 };
 
 // Local greedy of part p (Alg. 4, one sender), run as the lazy greedy of
@@ -659,15 +661,38 @@ __global__ void __launch_bounds__(kRGThreads) k_rg_stream_cluster(RGArgs a, int6
 // accepted subsets are then or-ed into the masks and the next group starts at
 // the cut.  Group sizes double after a group without a cut and halve after a
 // cut.
+// The slot whose work items hold item c: the largest u < gn with s_off[u] <= c.
 __device__ __forceinline__ int mask_slot_of(const int64_t *s_off, int gn, int64_t c) {
-    int u = 0;
-    while (u + 1 < gn && s_off[u + 1] <= c) ++u;
-    return u;
+    int lo = 0, hi = gn - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Exclusive prefix of the work items of slots [0, gn) (items[u] from f(u)),
+// written to s_off[0..gn]; gn <= 64, run by warp 0.
+template <typename F>
+__device__ __forceinline__ void mask_item_prefix(int64_t *s_off, int gn, F &&f) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const int u0 = 2 * lane, u1 = 2 * lane + 1;
+    const int64_t a0 = u0 < gn ? f(u0) : 0, a1 = u1 < gn ? f(u1) : 0;
+    const int64_t incl = warp_incl_scan<int64_t>(a0 + a1, lane);
+    const int64_t excl = incl - a0 - a1;
+    if (u0 < gn) s_off[u0] = excl;
+    if (u1 < gn) s_off[u1] = excl + a0;
+    if (lane == 31) s_off[gn] = incl;
 }
 
 __global__ void __launch_bounds__(kRGThreads) k_rg_stream_masks(RGArgs a) {
     __shared__ int32_t s_x[kMaskG];
     __shared__ int64_t s_beg[kMaskG], s_len[kMaskG];
+    __shared__ uint32_t s_g[kMaskG * 64];            // the group's gains, staged once
+    __shared__ unsigned long long s_pass[64];        // slots reaching each bucket's threshold
+    __shared__ int64_t s_thr[64];
     __shared__ int64_t s_off[kMaskG + 1];            // work-item prefix over the group's slots
     __shared__ unsigned long long s_acc[kMaskG];     // buckets accepting each slot
     __shared__ int32_t s_n[64];
@@ -677,12 +702,24 @@ __global__ void __launch_bounds__(kRGThreads) k_rg_stream_masks(RGArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t gwarp = gtid >> 5, nwarps = gstride >> 5;
+    // warps numbered block-minor, so the few work items of a small group land
+    // on different SMs
+    const int64_t gwarp = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int64_t nwarps = gstride >> 5;
     const int64_t nslots = (int64_t)a.trunc * a.P;
     const uint64_t t_begin = global_ns();
     for (int64_t i = gtid; i < a.theta; i += gstride) a.mask[i] = 0ull;
     for (int64_t i = gtid; i < 2 * kMaskG * 64; i += gstride) a.gbuf[i] = 0u;
+    // slot table: element (or -1) and its covering-subset range, read once
+    for (int64_t t = gtid; t < nslots; t += gstride) {
+        const int32_t x = ld_acquire_u32(a.flags + t) == 1u ? __ldcg(a.elems + t) : -1;
+        const int64_t b = x >= 0 ? a.vtx_off[x] : 0;
+        a.slot_x[t] = x;
+        a.slot_beg[t] = b;
+        a.slot_len[t] = x >= 0 ? a.vtx_off[x + 1] - b : 0;
+    }
     if (threadIdx.x < 64) {
+        s_thr[threadIdx.x] = threadIdx.x < a.B ? a.thr[threadIdx.x] : 0;
         s_n[threadIdx.x] = 0;
         s_cov[threadIdx.x] = 0;
         s_eval[threadIdx.x] = 0;
@@ -695,23 +732,14 @@ __global__ void __launch_bounds__(kRGThreads) k_rg_stream_masks(RGArgs a) {
         const int gn = (int)(nslots - g0 < G ? nslots - g0 : G);
         if (threadIdx.x < gn) {
             const int64_t t = g0 + threadIdx.x;
-            const int32_t x = ld_acquire_u32(a.flags + t) == 1u ? __ldcg(a.elems + t) : -1;
-            s_x[threadIdx.x] = x;
-            const int64_t b = x >= 0 ? a.vtx_off[x] : 0;
-            s_beg[threadIdx.x] = b;
-            s_len[threadIdx.x] = x >= 0 ? a.vtx_off[x + 1] - b : 0;
+            s_x[threadIdx.x] = __ldcg(a.slot_x + t);
+            s_beg[threadIdx.x] = __ldcg(a.slot_beg + t);
+            s_len[threadIdx.x] = __ldcg(a.slot_len + t);
             s_acc[threadIdx.x] = 0ull;
         }
         if (threadIdx.x == 0) s_cut = gn;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int64_t c = 0;
-            for (int u = 0; u < gn; ++u) {
-                s_off[u] = c;
-                c += (s_len[u] + kMaskItem - 1) / kMaskItem;
-            }
-            s_off[gn] = c;
-        }
+        mask_item_prefix(s_off, gn, [&](int u) { return (s_len[u] + kMaskItem - 1) / kMaskItem; });
         __syncthreads();
         uint32_t *gb = a.gbuf + (size_t)buf * kMaskG * 64;
         // ---- counts of every slot of the group against the current masks
@@ -720,13 +748,22 @@ __global__ void __launch_bounds__(kRGThreads) k_rg_stream_masks(RGArgs a) {
             const int64_t e0 = (c - s_off[u]) * kMaskItem;
             const int64_t len = s_len[u];
             const int32_t *ids = a.set_ids + s_beg[u];
-            // 5-bit vertical counters, one bit-plane per 64-bit word
-            unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
-#pragma unroll 4
+            // all ids first, then all masks: two memory round trips per item
+            int32_t id[kMaskStrips];
+#pragma unroll
             for (int st = 0; st < kMaskStrips; ++st) {
                 const int64_t e = e0 + st * 32 + lane;
-                unsigned long long m = 0ull;
-                if (e < len) m = ~__ldcg(a.mask + __ldg(ids + e));
+                id[st] = e < len ? __ldg(ids + e) : -1;
+            }
+            unsigned long long mk[kMaskStrips];
+#pragma unroll
+            for (int st = 0; st < kMaskStrips; ++st)
+                mk[st] = id[st] >= 0 ? ~__ldcg(a.mask + id[st]) : 0ull;
+            // 5-bit vertical counters, one bit-plane per 64-bit word
+            unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+#pragma unroll
+            for (int st = 0; st < kMaskStrips; ++st) {
+                unsigned long long m = mk[st];
                 unsigned long long t = c0 & m;
                 c0 ^= m;
                 m = t;
@@ -741,80 +778,96 @@ __global__ void __launch_bounds__(kRGThreads) k_rg_stream_masks(RGArgs a) {
                 m = t;
                 c4 |= m;
             }
-            for (int b = 0; b < a.B; ++b) {
-                const uint32_t v = __popc(__ballot_sync(kFull, (c0 >> b) & 1ull)) +
-                                   (__popc(__ballot_sync(kFull, (c1 >> b) & 1ull)) << 1) +
-                                   (__popc(__ballot_sync(kFull, (c2 >> b) & 1ull)) << 2) +
-                                   (__popc(__ballot_sync(kFull, (c3 >> b) & 1ull)) << 3) +
-                                   (__popc(__ballot_sync(kFull, (c4 >> b) & 1ull)) << 4);
-                if (lane == (b & 31) && v) atomicAdd(gb + u * 64 + b, v);
+            // add the 32 lanes' counters bit-serially in a butterfly: after
+            // round r every lane holds the sum over its 2^(r+1)-lane group
+            unsigned long long pl[10] = {c0, c1, c2, c3, c4, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                unsigned long long carry = 0;
+#pragma unroll
+                for (int q = 0; q < 5 + r; ++q) {
+                    const unsigned long long x = pl[q];
+                    const unsigned long long y = __shfl_xor_sync(kFull, x, 1 << r);
+                    pl[q] = x ^ y ^ carry;
+                    carry = (x & y) | (carry & (x ^ y));
+                }
+                pl[5 + r] = carry;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int b = lane + 32 * h;
+                uint32_t v = 0;
+#pragma unroll
+                for (int q = 0; q < 10; ++q) v |= (uint32_t)((pl[q] >> b) & 1ull) << q;
+                if (b < a.B && v) atomicAdd(gb + u * 64 + b, v);
             }
         }
         if (!grid_sync(a.bar, gridDim.x, a.status)) return;
-        // ---- the sequential rule of every bucket, replayed in every block
+        // ---- the sequential rule of every bucket, replayed in every block.
+        // Within a group a bucket takes at most its first passing slot: a
+        // second one (while the bucket still has room) needs a fresh count,
+        // so the group is cut there.
+        if (threadIdx.x < 64) s_pass[threadIdx.x] = 0ull;
+        __syncthreads();
+        for (int i = threadIdx.x; i < gn * 64; i += blockDim.x) {
+            const uint32_t g = __ldcg(gb + i);
+            s_g[i] = g;
+            const int u = i >> 6, b = i & 63;
+            if (b < a.B && s_x[u] >= 0 && (int64_t)g >= s_thr[b]) atomicOr(&s_pass[b], 1ull << u);
+        }
+        __syncthreads();
         const int b = threadIdx.x;
-        const bool own = b < a.B;
-        const int64_t T = own ? a.thr[b] : 0;
-        if (own) {
-            int32_t nb = s_n[b];
-            bool took = false;
-            for (int u = 0; u < gn && nb < a.k; ++u) {
-                if (s_x[u] < 0) continue;
-                if ((int64_t)__ldcg(gb + u * 64 + b) >= T) {
-                    if (took) {
-                        atomicMin(&s_cut, u);
-                        break;
-                    }
-                    took = true;
-                    ++nb;
-                }
-            }
+        const bool own = b < a.B && s_n[b] < a.k;
+        int first = kMaskG;
+        if (own && s_pass[b]) {
+            const unsigned long long pm = s_pass[b];
+            first = __ffsll((long long)pm) - 1;
+            const unsigned long long rest = pm & (pm - 1);
+            if (rest && s_n[b] + 1 < a.k) atomicMin(&s_cut, __ffsll((long long)rest) - 1);
         }
         __syncthreads();
         const int cut = s_cut;
         if (own) {
-            int32_t nb = s_n[b];
-            int64_t cov = s_cov[b];
-            for (int u = 0; u < cut && nb < a.k; ++u) {
-                if (s_x[u] < 0) continue;
-                const int64_t g = (int64_t)__ldcg(gb + u * 64 + b);
-                ++s_eval[b];
-                s_scan[b] += s_len[u];
-                if (g >= T) {
-                    atomicOr(&s_acc[u], 1ull << b);
-                    if (blockIdx.x == 0) {
-                        a.bucket_seeds[(int64_t)b * a.k + nb] = s_x[u];
-                        a.bucket_gains[(int64_t)b * a.k + nb] = g;
-                    }
-                    ++nb;
-                    cov += g;
+            if (first < cut) {
+                const int64_t g = (int64_t)s_g[first * 64 + b];
+                atomicOr(&s_acc[first], 1ull << b);
+                if (blockIdx.x == 0) {
+                    a.bucket_seeds[(int64_t)b * a.k + s_n[b]] = s_x[first];
+                    a.bucket_gains[(int64_t)b * a.k + s_n[b]] = g;
                 }
+                ++s_n[b];
+                s_cov[b] += g;
             }
-            s_n[b] = nb;
-            s_cov[b] = cov;
+            // diagnostics: slots this bucket considered (up to the cut, or to
+            // its accept when that filled it)
+            const int last = (first < cut && s_n[b] == a.k) ? first + 1 : cut;
+            for (int u = 0; u < last; ++u)
+                if (s_x[u] >= 0) {
+                    ++s_eval[b];
+                    s_scan[b] += s_len[u];
+                }
         }
         __syncthreads();
         // ---- or the accepted subsets into the masks; clear the other buffer
-        if (threadIdx.x == 0) {
-            int64_t c = 0;
-            for (int u = 0; u < cut; ++u) {
-                s_off[u] = c;
-                if (s_acc[u]) c += (s_len[u] + kMaskItem - 1) / kMaskItem;
-            }
-            s_off[cut] = c;
-        }
+        mask_item_prefix(s_off, cut, [&](int u) {
+            return s_acc[u] ? (s_len[u] + kMaskItem - 1) / kMaskItem : (int64_t)0;
+        });
         __syncthreads();
         for (int64_t c = gwarp; c < s_off[cut]; c += nwarps) {
-            int u = 0;
-            while (u + 1 < cut && (s_off[u + 1] <= c || !s_acc[u])) ++u;
+            const int u = mask_slot_of(s_off, cut, c);   // slots without items are skipped
             const unsigned long long acc = s_acc[u];
             const int64_t e0 = (c - s_off[u]) * kMaskItem;
             const int64_t len = s_len[u];
             const int32_t *ids = a.set_ids + s_beg[u];
+            int32_t id[kMaskStrips];
+#pragma unroll
             for (int st = 0; st < kMaskStrips; ++st) {
                 const int64_t e = e0 + st * 32 + lane;
-                if (e < len) atomicOr(a.mask + __ldg(ids + e), acc);
+                id[st] = e < len ? __ldg(ids + e) : -1;
             }
+#pragma unroll
+            for (int st = 0; st < kMaskStrips; ++st)
+                if (id[st] >= 0) atomicOr(a.mask + id[st], acc);
         }
         uint32_t *other = a.gbuf + (size_t)(buf ^ 1) * kMaskG * 64;
         for (int64_t i = gtid; i < kMaskG * 64; i += gstride) other[i] = 0u;
@@ -1044,6 +1097,9 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     const size_t o_mask = use_masks ? take((size_t)std::max<int64_t>(theta, 1) * 8) : 0;
     const size_t o_gbuf = use_masks ? take((size_t)2 * kMaskG * 64 * 4) : 0;
     const size_t o_bar = use_masks ? take(sizeof(GridBarrier)) : 0;
+    const size_t o_sx = use_masks ? take((size_t)trunc * P * 4) : 0;
+    const size_t o_sb = use_masks ? take((size_t)trunc * P * 8) : 0;
+    const size_t o_sl = use_masks ? take((size_t)trunc * P * 8) : 0;
     void *base = nullptr;
     s = pool_scratch(p, off, &base);
     if (s != IM_OK) return s;
@@ -1098,6 +1154,9 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     a.mask = use_masks ? (unsigned long long *)(Bs + o_mask) : nullptr;
     a.gbuf = use_masks ? (uint32_t *)(Bs + o_gbuf) : nullptr;
     a.bar = use_masks ? (GridBarrier *)(Bs + o_bar) : nullptr;
+    a.slot_x = use_masks ? (int32_t *)(Bs + o_sx) : nullptr;
+    a.slot_beg = use_masks ? (int64_t *)(Bs + o_sb) : nullptr;
+    a.slot_len = use_masks ? (int64_t *)(Bs + o_sl) : nullptr;
     if (use_masks) IM_CUDA(cudaMemsetAsync(Bs + o_bar, 0, sizeof(GridBarrier), st));
 
     IM_CUDA(cudaFuncSetAttribute(k_randgreedi, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -233,3 +233,59 @@ def graph_livejournal_like(seed: int = 42) -> Graph:
 def graph_orkut_like(seed: int = 42) -> Graph:
     """Orkut-shaped R-MAT (3,072,441 vertices, 234,369,798 edges), IC p = 0.01."""
     return rmat_graph(3072441, 234_369_798, seed, "ic0.01", levels=22)
+
+
+# --- many queries: the batched mix and the served arrival trace -------------
+
+BATCH_SCALES = tuple(range(12, 19))
+
+
+def batched_graph(scale: int, seed: int = 42) -> Graph:
+    """R-MAT graph of the batched mix: 2^scale vertices, edge factor 16, weights
+    1/in-degree (LT weights, and the weighted-cascade IC probabilities)."""
+    return rmat_graph(1 << scale, 16 << scale, seed, "lt")
+
+
+@dataclass
+class QuerySpec:
+    """One influence-maximization query of a synthetic workload."""
+    graph: str          # "rmat<scale>" or "orkut"
+    model: int          # 0 IC, 1 LT
+    k: int
+    theta: int
+    seed: int
+    arrival_s: float = 0.0
+
+
+def batched_queries(nq: int = 256, seed: int = 42) -> list[QuerySpec]:
+    """The batched mix: per query a scale uniform in 12..18, IC or LT with
+    probability 1/2 each, k uniform in [5, 100], theta uniform in
+    [2^14, 2^20] and its own Philox seed (numpy PCG64 draws keyed by seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x717565727921))
+    out = []
+    for q in range(nq):
+        scale = int(rng.integers(12, 19))
+        model = int(rng.integers(0, 2))
+        k = int(rng.integers(5, 101))
+        theta = int(rng.integers(1 << 14, (1 << 20) + 1))
+        qseed = (seed ^ ((q + 1) * 0x9E3779B97F4A7C15)) & ((1 << 64) - 1)
+        out.append(QuerySpec(f"rmat{scale}", model, k, theta, qseed))
+    return out
+
+
+def served_trace(nq: int = 512, seed: int = 42, rate_per_s: float = 200.0,
+                 orkut_frac: float = 0.05) -> list[QuerySpec]:
+    """Poisson arrivals (exponential gaps, mean 1/rate) of queries drawn like
+    the batched mix; a fraction orkut_frac of them runs on the Orkut-shaped
+    graph (IC p = 0.01) with theta uniform in [2^6, 2^10] (the mix's range
+    divided by 256: an Orkut-shaped RRR set averages ~6e4 members)."""
+    base = batched_queries(nq, seed + 1)
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x6172726976616c))
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=nq))
+    for q, spec in enumerate(base):
+        spec.arrival_s = float(t[q])
+        if rng.random() < orkut_frac:
+            spec.graph = "orkut"
+            spec.model = 0
+            spec.theta = int(rng.integers(1 << 6, (1 << 10) + 1))
+    return base

@@ -154,3 +154,16 @@ def test_rmat_fixture_shape():
     assert np.all(np.diff(key) > 0)          # sorted by (dst, src), no repeats
     assert g.digest() == inputs.graph_small_ic().digest()
     assert np.all(g.w == inputs.quantise_probability(0.1)) and int(g.w[0]) == 429496730
+
+
+def test_parallel_split_equals_one_call(orc):
+    """The process-parallel oracle (id ranges split over spawned workers) gives
+    exactly the single call's pool: sample ids key every draw."""
+    from oracle import parallel
+    g = inputs.rmat_graph(1 << 12, 1 << 16, 5, "lt")
+    for model in (orc.IC, orc.LT):
+        one = orc.sample(model, g, 11, 100, 5000)
+        par = parallel.sample(model, g, 11, 100, 5000, workers=3, chunk=777)
+        assert np.array_equal(one.set_off, par.set_off)
+        assert np.array_equal(one.members, par.members)
+        assert one.examined == par.examined
