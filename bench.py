@@ -61,8 +61,12 @@ WORKLOAD = ("rmat20-lt: R-MAT scale 20 (1,048,576 vertices, 16,777,216 edges, a/
             "seed 42), LT 1/in-degree as uint32, theta=4,194,304 RRR sets, k=100; plain greedy "
             "+ RandGreedi (148 partitions, streamed top ceil(k/4), delta=0.077)")
 # DRAM bytes per launch from an ncu capture, valid while the kernel source is
-# unchanged (sha256 of the file that holds it).
-TRAFFIC: dict = {}
+# unchanged (sha256 of the file that holds it).  k_sample_lt1 was captured on
+# the same graph at theta = 1,048,576 (42.82 M walk steps, 5.488 GB read +
+# written, profiles/ncu_sample_lt1_rmat20_theta1M.txt); traffic grows with the
+# walk steps, so a full launch (171.49 M steps) moves 5.488 * 171.49 / 42.82 GB.
+TRAFFIC: dict = {"sample_lt": {"src_sha": "96bc70f09ae66c68",
+                               "bytes_per_launch": int(5.488e9 * 171.49 / 42.82)}}
 
 
 def parse():
@@ -307,16 +311,20 @@ def run_ours(args):
             "phase_ms": {k: round(v[1], 3) for k, v in sorted(per.items())},
             "gpu_launches": launches, "roofline": roofline, "clocks": clk}
 
+    pool_stats = cover_stats(im, pool, g.n, theta, K, opts_rg)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["bit_exact"], line["cpu_baseline"] = cpu_baseline_and_check(g, pool, first)
     if not args.no_e2e:
         line["e2e"] = e2e(args, g, im, torch, dev, stream, first, dist)
     pool.close()
     G.close()
+    line["kernels"] = kernel_rooflines(im, pool_stats, per, hbm)
     if not args.no_extras:
         line["batched"] = bench_batched(im, torch)
         line["served"] = bench_served(im, torch, args.served_orkut)
-        line["ic"] = bench_ic(im, torch)
+        lj = inputs.graph_livejournal_like_both(SEED)
+        line["ic"] = bench_ic(im, torch, lj["trivalency"])
+        line["imm"] = bench_imm(im, torch, lj["wc"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -383,7 +391,54 @@ def e2e(args, g, im, torch, dev, stream, first, dist):
 
 
 # ---------------------------------------------------------------------------
-# IC sampling, batched queries, served queries
+# per-kernel rooflines
+# ---------------------------------------------------------------------------
+
+def cover_stats(im, pool, n, theta, k, opts_rg):
+    """Counts the algorithmic-byte formulas of the index and cover kernels need:
+    T, sum over the greedy's seeds of |S(v)|, sum over the sets it covers of
+    |R(i)| and their number, and the RandGreedi producers' scanned entries."""
+    set_off, _ = pool.export()
+    vtx_off, set_ids = pool.index()
+    c = pool.cover(k)
+    sizes = np.diff(set_off)
+    seeds = c.seeds.astype(np.int64)
+    s_seed = int(np.sum(vtx_off[seeds + 1] - vtx_off[seeds]))
+    covered = np.unique(np.concatenate([set_ids[vtx_off[v]:vtx_off[v + 1]] for v in seeds])) \
+        if len(seeds) else np.zeros(0, np.int64)
+    pool.cover(k, opts_rg)
+    st = im.im_randgreedi_stats(pool.handle, PARTS, 63)
+    return {"T": int(set_off[-1]), "n": n, "theta": theta, "k": k, "s_seed": s_seed,
+            "covered": int(covered.size), "r_covered": int(np.sum(sizes[covered])),
+            "rg_eval": int(st[:PARTS, 4].sum()), "rg_cover": int(st[:PARTS, 5].sum())}
+
+
+def kernel_rooflines(im, cs, per, hbm):
+    """Achieved GB/s and fraction of measured HBM of the step's kernels, from
+    the algorithmic-byte formulas of each (see the design notes) and the
+    kernels' CUDA-event times inside the timed region."""
+    T, n, th, k = cs["T"], cs["n"], cs["theta"], cs["k"]
+    alg = {
+        "sort_sets_warp": 8 * T + 16 * th,
+        "index_hist": 12 * T,
+        "index_scatter": 16 * T + 16 * th,
+        "greedy": 4 * n * k + 4 * cs["s_seed"] + 16 * cs["covered"] + 12 * cs["r_covered"] + th // 8,
+        "randgreedi_local": 4 * (cs["rg_eval"] + cs["rg_cover"]) + PARTS * th // 8,
+    }
+    out = {}
+    for name, (launches, ms) in sorted(per.items()):
+        if ms <= 0.05:
+            continue
+        e = {"ms": round(ms, 3)}
+        if name in alg and launches > 0:
+            gbs = alg[name] / (ms / 1000.0) / 1e9
+            e.update({"alg_bytes": int(alg[name]), "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4)})
+        out[name] = e
+    return out
+
+
+# ---------------------------------------------------------------------------
+# IC sampling, IMM, batched queries, served queries
 # ---------------------------------------------------------------------------
 
 class OneQuery:
@@ -524,9 +579,33 @@ def bench_served(im, torch, orkut: bool):
             "bit_exact_vs_plain": bool(same)}
 
 
-def bench_ic(im, torch):
+def bench_imm(im, torch, g):
+    """IMM (Alg. 1) through im_solve on the LiveJournal-shaped graph, IC with
+    weighted-cascade probabilities, eps = 0.13, l = 1, k = 200."""
+    G = im.Graph(g)
+    im.im_solve(G.handle, im.IM_IC, 200, 0.5, 1.0, SEED + 1)   # warm-up (LT-free, small)
+    torch.cuda.synchronize()
+    im.im_profile_reset()
+    im.im_profile_enable(True)
+    t0 = time.perf_counter()
+    seeds, cov, theta, info = im.im_solve(G.handle, im.IM_IC, 200, 0.13, 1.0, SEED)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    im.im_profile_enable(False)
+    prof = im.im_profile_read()
+    G.close()
+    return {"workload": "LiveJournal-shaped R-MAT (4,847,571 vertices, 69,000,000 edges), IC "
+                        "weighted cascade (1/in-degree), eps=0.13, l=1, k=200",
+            "ms": round(1000 * dt, 2), "rounds": int(info.rounds),
+            "theta_rounds": [int(x) for x in info.theta_rounds[:info.rounds]],
+            "lb": info.lb, "theta": int(theta), "round_entries": int(info.round_entries),
+            "final_entries": int(info.final_entries), "coverage": int(cov),
+            "num_seeds": int(len(seeds)), "final_examined_edges": int(info.examined),
+            "phase_ms": {k: round(v[1], 3) for k, v in sorted(prof.items())}}
+
+
+def bench_ic(im, torch, g):
     """IC sampling on the LiveJournal-shaped graph (trivalency), 8,192 sets."""
-    g = inputs.graph_livejournal_like(SEED)
     G = im.Graph(g)
     theta = 8192
     p = im.Pool(G, theta, theta * 600_000)

@@ -179,13 +179,37 @@ __global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
                 const uint32_t bit = 1u << (i & 31);
                 fresh = !(atomicOr(&a.covered[i >> 5], bit) & bit);
             }
-            unsigned fm = __ballot_sync(kFull, fresh);
-            while (fm) {
-                const int f = __ffs(fm) - 1;
-                fm &= fm - 1;
-                const int32_t set = __shfl_sync(kFull, i, f);
-                const int64_t so = a.set_off[set], eo = a.set_off[set + 1];
-                for (int64_t q = so + lane; q < eo; q += 32) atomicSub(&a.counts[a.members[q]], 1);
+            if (!__any_sync(kFull, fresh)) continue;
+            // decrement the gains of every member of the lane's newly covered
+            // set: the warp walks the concatenation of those member lists 32
+            // entries at a time, several loads in flight per lane
+            int64_t mo = 0, ml = 0;
+            if (fresh) {
+                mo = a.set_off[i];
+                ml = a.set_off[i + 1] - mo;
+            }
+            const int64_t incl = warp_incl_scan<int64_t>(ml, lane);
+            const int64_t tot = __shfl_sync(kFull, incl, 31);
+            constexpr int U = 4;
+            for (int64_t p0 = 0; p0 < tot; p0 += 32 * U) {
+                int32_t mv[U];
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu) {
+                    const int64_t q = p0 + uu * 32 + lane;
+                    int owner = 0;               // first lane whose inclusive count exceeds q
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
+                        if (c <= q) owner += step;
+                    }
+                    const int64_t o_incl = __shfl_sync(kFull, incl, owner);
+                    const int64_t o_ml = __shfl_sync(kFull, ml, owner);
+                    const int64_t o_mo = __shfl_sync(kFull, mo, owner);
+                    mv[uu] = q < tot ? __ldg(a.members + o_mo + (q - (o_incl - o_ml))) : -1;
+                }
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu)
+                    if (mv[uu] >= 0) atomicSub(&a.counts[mv[uu]], 1);
             }
         }
         if (!grid_sync(a.bar, nb, a.status)) return;

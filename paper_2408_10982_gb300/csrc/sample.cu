@@ -740,6 +740,58 @@ __device__ __forceinline__ Key warp_bitonic32(Key v, int lane) {
     return v;
 }
 
+// Bitonic sort of 32 E keys held by a warp in registers, element i = r 32 +
+// lane in v[r] (the layout of a coalesced load).  Partners i ^ j with j < 32
+// sit in other lanes (shuffle), with j >= 32 in the same lane (registers).
+template <typename Key, int E>
+__device__ __forceinline__ void warp_bitonic_regs(Key (&v)[E], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jr = j >> 5;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    if (r & jr) continue;
+                    const int r2 = r | jr;
+                    const bool asc = (((r << 5) | lane) & k) == 0;
+                    const Key x = v[r], y = v[r2];
+                    const bool sw = asc ? (y < x) : (x < y);
+                    v[r] = sw ? y : x;
+                    v[r2] = sw ? x : y;
+                }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const bool asc = (((r << 5) | lane) & k) == 0;
+                    const Key x = v[r];
+                    const Key y = __shfl_xor_sync(kFull, x, j);
+                    const Key lo = y < x ? y : x, hi = y < x ? x : y;
+                    v[r] = (lower == asc) ? lo : hi;
+                }
+            }
+        }
+    }
+}
+
+template <typename Key, int E>
+__device__ __forceinline__ void warp_sort_copy(Key *out, const Key *src, int64_t len, int lane) {
+    Key v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int64_t t = (int64_t)r * 32 + lane;
+        v[r] = t < len ? src[t] : key_max<Key>();
+    }
+    warp_bitonic_regs<Key, E>(v, lane);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int64_t t = (int64_t)r * 32 + lane;
+        if (t < len) out[t] = v[r];
+    }
+}
+
 // bitonic network over buf[0..P) (P a power of two) by `nthreads` threads
 template <typename Key>
 __device__ __forceinline__ void bitonic_smem(Key *buf, int P, int tid, int nthreads,
@@ -784,6 +836,14 @@ __global__ void __launch_bounds__(256) k_sort_small(Key *dst, const int64_t *seg
             Key v = lane < len ? src[lane] : key_max<Key>();
             v = warp_bitonic32<Key>(v, lane);
             if (lane < len) out[lane] = v;
+        } else if (len <= 64) {
+            warp_sort_copy<Key, 2>(out, src, len, lane);
+        } else if (len <= 128) {
+            warp_sort_copy<Key, 4>(out, src, len, lane);
+        } else if (len <= 256) {
+            warp_sort_copy<Key, 8>(out, src, len, lane);
+        } else if (len <= 512 && sizeof(Key) == 4) {
+            warp_sort_copy<Key, 16>(out, src, len, lane);
         } else if (len <= kCapW) {
             int P = 64;
             while (P < len) P <<= 1;

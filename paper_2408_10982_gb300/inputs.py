@@ -230,6 +230,15 @@ def graph_livejournal_like(seed: int = 42) -> Graph:
     return rmat_graph(4847571, 69_000_000, seed, "trivalency", levels=23)
 
 
+def graph_livejournal_like_both(seed: int = 42) -> dict:
+    """The LiveJournal-shaped topology once, with two weightings sharing it:
+    "trivalency" (IC) and "wc" (IC weighted cascade, 1/in-degree)."""
+    src, dst = rmat_edges(4847571, 69_000_000, seed=seed, levels=23)
+    in_off, in_src = in_csr(4847571, src, dst)
+    return {"trivalency": Graph(4847571, in_off, in_src, weights_trivalency(69_000_000, seed)),
+            "wc": Graph(4847571, in_off, in_src, weights_inverse_indegree(in_off))}
+
+
 def graph_orkut_like(seed: int = 42) -> Graph:
     """Orkut-shaped R-MAT (3,072,441 vertices, 234,369,798 edges), IC p = 0.01."""
     return rmat_graph(3072441, 234_369_798, seed, "ic0.01", levels=22)
