@@ -195,8 +195,20 @@ im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
  *                       in the shared memory of a cluster of at least that
  *                       many blocks (the smallest of 1, 2, 4, 8 that holds
  *                       it); -1 keeps the bitmaps in global memory (one block
- *                       per bucket). */
-typedef enum { IM_TUNE_LT_GROUP = 0, IM_TUNE_RG_CLUSTER = 1 } im_tune_knob;
+ *                       per bucket).
+ *   IM_TUNE_INDEX_REPLICAS  covering-subset build: per-vertex counters and
+ *                       cursors replicated 1, 2, 4 (default) or 8 times (a member's
+ *                       replica follows its position), spreading the atomics
+ *                       on hub vertices; the order of set ids inside an S(v)
+ *                       is unspecified in every case.
+ *   IM_TUNE_RG_EVALS    RandGreedi local greedy: candidates re-evaluated per
+ *                       round, 1, 2 (default), 4 or 8. */
+typedef enum {
+    IM_TUNE_LT_GROUP = 0,
+    IM_TUNE_RG_CLUSTER = 1,
+    IM_TUNE_INDEX_REPLICAS = 2,
+    IM_TUNE_RG_EVALS = 3
+} im_tune_knob;
 im_status im_tune_set(int32_t knob, int64_t value);
 im_status im_tune_get(int32_t knob, int64_t *value);
 

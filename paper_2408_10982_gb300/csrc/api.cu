@@ -97,12 +97,13 @@ KernelTimer::~KernelTimer() {
 
 namespace {
 std::mutex g_tune_mu;
-int64_t g_tune[2] = {1, 0};   // IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER
+// IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER, IM_TUNE_INDEX_REPLICAS, IM_TUNE_RG_EVALS
+int64_t g_tune[4] = {1, 0, 4, 2};
 }  // namespace
 
 int64_t tune_value(int32_t knob) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    return (knob >= 0 && knob < 2) ? g_tune[knob] : 0;
+    return (knob >= 0 && knob < 4) ? g_tune[knob] : 0;
 }
 
 int num_sms() {
@@ -351,7 +352,7 @@ im_status im_pool_create(const im_graph *g, int64_t max_sets, int64_t max_entrie
         (e = cudaMalloc(&p->vtx_off, (size_t)(n + 1) * 8)) != cudaSuccess ||
         (e = cudaMalloc(&p->set_ids, (size_t)std::max<int64_t>(max_entries, 1) * 4)) !=
             cudaSuccess ||
-        (e = cudaMalloc(&p->vtx_cursor, (size_t)n * 4)) != cudaSuccess) {
+        (e = cudaMalloc(&p->vtx_cursor, (size_t)(kMaxIndexReplicas + 1) * n * 4)) != cudaSuccess) {
         im_status s = cuda_fail(e, "im_pool_create: cudaMalloc");
         im_pool_destroy(p);
         return s;
@@ -550,7 +551,11 @@ im_status im_tune_set(int32_t knob, int64_t value) {
     const bool ok = (knob == IM_TUNE_LT_GROUP && (value == 1 || value == 8 || value == 16 || value == 32)) ||
                     (knob == IM_TUNE_RG_CLUSTER &&
                      (value == -1 || value == 0 || value == 1 || value == 2 || value == 4 ||
-                      value == 8));
+                      value == 8)) ||
+                    (knob == IM_TUNE_INDEX_REPLICAS && (value == 1 || value == 2 || value == 4 ||
+                                                        value == 8)) ||
+                    (knob == IM_TUNE_RG_EVALS && (value == 1 || value == 2 || value == 4 ||
+                                                  value == 8));
     if (ok) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[knob] = value;
@@ -561,7 +566,7 @@ im_status im_tune_set(int32_t knob, int64_t value) {
 }
 
 im_status im_tune_get(int32_t knob, int64_t *value) {
-    if (!value || (knob != IM_TUNE_LT_GROUP && knob != IM_TUNE_RG_CLUSTER))
+    if (!value || knob < IM_TUNE_LT_GROUP || knob > IM_TUNE_RG_EVALS)
         return IM_ERR_INVALID_ARG;
     *value = tune_value(knob);
     return IM_OK;

@@ -418,7 +418,7 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
         int64_t *vtx_off = (int64_t *)(A + o_voff);
         int32_t *set_ids = (int32_t *)(A + o_sids);
         s = build_index_raw(set_off, members, sets_total, added, n_total, vtx_off, set_ids,
-                            (int32_t *)(A + o_cur), tmp, st);
+                            (int32_t *)(A + o_cur), 1, tmp, st);
         if (s != IM_OK) return s;
         // 4. one greedy launch, a block per query
         int32_t *d_seeds = (int32_t *)(A + o_out);

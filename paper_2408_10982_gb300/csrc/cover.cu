@@ -246,6 +246,7 @@ struct RGArgs {
     int32_t nprod, ncons;     // block roles in this launch
     int32_t first_role;       // 0: blocks start with producers; 1: consumers only
     int32_t max_np;           // largest part: key[] and stamp[] are max_np each
+    int32_t evals;            // local greedy: candidates re-evaluated per round (<= kProdW)
     long long *stats;         // [P + B][6] diagnostics (see im_randgreedi_stats)
     int *status;
     // bucket-mask stage (k_rg_stream_masks)
@@ -259,15 +260,42 @@ struct RGArgs {
 // Local greedy of part p (Alg. 4, one sender), run as the lazy greedy of
 // Alg. 2: key[l] holds a gain of candidate l that is exact when stamp[l]
 // equals the current round and an upper bound otherwise (gains only shrink,
-// by submodularity).  A round takes the largest key (ties: smallest id); a
-// fresh winner is the true argmax and is taken, a stale one is re-evaluated
-// against the partition's covered bitmap and the round retried.  This picks
-// exactly the standard greedy's sequence, and needs no member lists of R(i).
+// by submodularity).  The largest key (ties: smallest id) is taken when it is
+// exact, which picks exactly the standard greedy's sequence.
+//
+// cmax[c] is the largest packed key (gain << 32 | ~l) of the 32 candidates of
+// chunk c.  A round takes the best candidate of each of the kProdW chunks with
+// the largest cmax and re-evaluates the stale ones at once (blockDim / kProdW
+// threads each) against the part's covered bitmap; then, if the overall
+// largest key is exact, it is taken.  Evaluating more candidates than the
+// sequential rule would only replaces upper bounds by exact values, so the
+// sequence of picks is unchanged while a pick takes one or two rounds instead
+// of one round per stale candidate.
+constexpr int kProdW = 8;
+
+__device__ __forceinline__ unsigned long long prod_key(int32_t g, int32_t l) {
+    return g > 0 ? ((unsigned long long)(uint32_t)g << 32) | (0xffffffffu - (uint32_t)l) : 0ull;
+}
+
+// cmax of chunk c, by one warp
+__device__ __forceinline__ void prod_chunk_max(const int32_t *key, unsigned long long *cmax,
+                                               int32_t np, int32_t c, int lane) {
+    const int32_t l = c * 32 + lane;
+    const unsigned long long v = warp_max_u64(l < np ? prod_key(key[l], l) : 0ull);
+    if (lane == 0) cmax[c] = v;
+}
+
 __device__ void produce(const RGArgs &a, int p, int32_t *key, unsigned long long *shm,
                         long long *shs) {
+    __shared__ int32_t s_cand[kProdW];
+    __shared__ int32_t s_cnt[kProdW];
+    __shared__ unsigned long long s_top;
     const int32_t vb = a.part_off[p], np = a.part_off[p + 1] - vb;
     const int32_t *vtx = a.part_vtx + vb;
     int32_t *stamp = key + a.max_np;
+    unsigned long long *cmax = reinterpret_cast<unsigned long long *>(key + 2 * a.max_np);
+    const int32_t nch = (np + 31) / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     uint32_t *cov = a.covered + (size_t)p * (size_t)a.words;
     for (int64_t x = threadIdx.x; x < a.words; x += blockDim.x) cov[x] = 0u;
     for (int32_t l = threadIdx.x; l < np; l += blockDim.x) {
@@ -276,43 +304,87 @@ __device__ void produce(const RGArgs &a, int p, int32_t *key, unsigned long long
         stamp[l] = 0;                                   // exact: nothing is covered yet
     }
     __syncthreads();
+    for (int32_t c = warp; c < nch; c += nwarp) prod_chunk_max(key, cmax, np, c, lane);
+    __syncthreads();
     const uint64_t t_begin = global_ns();
     long long n_rounds = 0, n_evals = 0, eval_entries = 0, cover_entries = 0;
     int64_t total = 0;
     int32_t j = 0;
+    const int W = a.evals;
+    const int gsz = blockDim.x / W, grp = threadIdx.x / gsz, gt = threadIdx.x % gsz;
     while (j < a.k) {
         ++n_rounds;
-        unsigned long long best = 0;
-        for (int32_t l = threadIdx.x; l < np; l += blockDim.x) {
-            const int32_t c = key[l];
-            if (c > 0) {
-                const unsigned long long kk =
-                    ((unsigned long long)(uint32_t)c << 32) | (0xffffffffu - (uint32_t)l);
-                best = kk > best ? kk : best;
+        // ---- the W chunks with the largest maxima (warp 0, by repeated max)
+        if (warp == 0) {
+            unsigned long long taken = 0ull;    // chunks already chosen, as keys
+            for (int w = 0; w < W; ++w) {
+                unsigned long long best = 0ull;
+                for (int32_t c = lane; c < nch; c += 32) {
+                    const unsigned long long v = cmax[c];
+                    // skip chunks chosen earlier this round (their keys are distinct)
+                    if (v > best && (w == 0 || v < taken)) best = v;
+                }
+                const unsigned long long m = warp_max_u64(best);
+                if (lane == 0) {
+                    s_cand[w] = m ? (int32_t)(0xffffffffu - (uint32_t)(m & 0xffffffffu)) : -1;
+                    s_cnt[w] = 0;
+                    if (w == 0) s_top = m;
+                }
+                taken = m;
+                if (!m) {
+                    for (int w2 = w + 1; w2 < W && lane == 0; ++w2) s_cand[w2] = -1;
+                    break;
+                }
             }
         }
-        best = block_max_u64(best, shm);
-        if (best == 0) break;                           // every gain is zero
-        const int32_t l = (int32_t)(0xffffffffu - (uint32_t)(best & 0xffffffffu));
+        __syncthreads();
+        if (s_top == 0ull) break;                       // every gain is zero
+        {
+            const int32_t l0 = s_cand[0];
+            if (stamp[l0] != j) {
+                // ---- re-evaluate every stale candidate of the round at once
+                const int32_t l = s_cand[grp];
+                const bool mine = l >= 0 && stamp[l] != j;
+                if (mine) {
+                    const int32_t v = vtx[l];
+                    const int64_t sb = a.vtx_off[v], se = a.vtx_off[v + 1];
+                    int miss = 0;
+                    scan_ids<4>(a.set_ids, sb, se - sb, gt, gsz, [&](int32_t i) {
+                        if (i >= 0) miss += !((__ldcg(cov + (i >> 5)) >> (i & 31)) & 1u);
+                    });
+                    miss = warp_sum<int>(miss);
+                    if (lane == 0 && miss) atomicAdd(&s_cnt[grp], miss);
+                }
+                __syncthreads();
+                if (mine && gt == 0) {
+                    key[l] = s_cnt[grp];
+                    stamp[l] = j;
+                    const int32_t v = vtx[l];
+                    ++n_evals;
+                    eval_entries += a.vtx_off[v + 1] - a.vtx_off[v];
+                }
+                __syncthreads();
+                // refresh the maxima of the chunks that changed, then the top
+                if (warp < W && s_cand[warp] >= 0)
+                    prod_chunk_max(key, cmax, np, s_cand[warp] >> 5, lane);
+                __syncthreads();
+                if (warp == 0) {
+                    unsigned long long best = 0ull;
+                    for (int32_t c = lane; c < nch; c += 32) best = cmax[c] > best ? cmax[c] : best;
+                    best = warp_max_u64(best);
+                    if (lane == 0) s_top = best;
+                }
+                __syncthreads();
+                if (s_top == 0ull) break;
+            }
+        }
+        const unsigned long long top = s_top;
+        const int32_t l = (int32_t)(0xffffffffu - (uint32_t)(top & 0xffffffffu));
+        if (stamp[l] != j) continue;                    // the top is still an upper bound
+        // ---- take it
         const int32_t v = vtx[l];
         const int64_t sb = a.vtx_off[v], se = a.vtx_off[v + 1];
-        if (stamp[l] != j) {
-            // stale: recompute |S(v) \ covered| and retry the round
-            long long miss = 0;
-            scan_ids<4>(a.set_ids, sb, se - sb, threadIdx.x, blockDim.x, [&](int32_t i) {
-                if (i >= 0) miss += !((__ldcg(cov + (i >> 5)) >> (i & 31)) & 1u);
-            });
-            const long long g = block_sum_i64(miss, shs);
-            if (threadIdx.x == 0) {
-                key[l] = (int32_t)g;
-                stamp[l] = j;
-            }
-            ++n_evals;
-            eval_entries += se - sb;
-            __syncthreads();
-            continue;
-        }
-        const int64_t gain = (int64_t)(best >> 32);
+        const int64_t gain = (int64_t)(top >> 32);
         if (threadIdx.x == 0) {
             a.local_seeds[(int64_t)p * a.k + j] = v;
             a.local_gains[(int64_t)p * a.k + j] = gain;
@@ -328,21 +400,27 @@ __device__ void produce(const RGArgs &a, int p, int32_t *key, unsigned long long
             if (i >= 0) atomicOr(&cov[i >> 5], 1u << (i & 31));
         });
         __syncthreads();
+        if (warp == 0) prod_chunk_max(key, cmax, np, l >> 5, lane);
+        __syncthreads();
         ++j;
     }
+    (void)shm;
+    (void)shs;
     if (threadIdx.x == 0) {
         a.local_n[p] = j;
         a.local_cov[p] = total;
         for (int32_t jj = j; jj < a.trunc; ++jj) st_release_u32(&a.flags[(int64_t)jj * a.P + p], 2u);
-        if (a.stats) {
-            long long *st = a.stats + 6 * (int64_t)p;
-            st[0] = (long long)t_begin;
-            st[1] = (long long)global_ns();
-            st[2] = n_rounds;
-            st[3] = n_evals;
-            st[4] = eval_entries;
-            st[5] = cover_entries;
-        }
+    }
+    n_evals = block_sum_i64(n_evals, shs);
+    eval_entries = block_sum_i64(eval_entries, shs);
+    if (threadIdx.x == 0 && a.stats) {
+        long long *st = a.stats + 6 * (int64_t)p;
+        st[0] = (long long)t_begin;
+        st[1] = (long long)global_ns();
+        st[2] = n_rounds;
+        st[3] = n_evals;
+        st[4] = eval_entries;
+        st[5] = cover_entries;
     }
     __syncthreads();
 }
@@ -1062,7 +1140,8 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     IM_CUDA(cudaStreamSynchronize(st));
     int32_t max_np = 0;
     for (int q = 0; q < P; ++q) max_np = std::max(max_np, hoff[q + 1] - hoff[q]);
-    const size_t prod_smem = (size_t)std::max(max_np, 1) * 8;   // key + stamp
+    // key + stamp (4 bytes each per candidate) + one 8-byte maximum per 32
+    const size_t prod_smem = (size_t)std::max(max_np, 1) * 8 + (size_t)((max_np + 31) / 32) * 8;
     if (prod_smem > 200 * 1024) {
         set_error("RandGreedi: a vertex part is too large for shared memory; use more partitions");
         return IM_ERR_UNSUPPORTED;
@@ -1174,6 +1253,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     a.elems = (int32_t *)(Bs + o_elems);
     a.status = d_status;
     a.max_np = std::max(max_np, 1);
+    a.evals = (int32_t)std::min<int64_t>(kProdW, std::max<int64_t>(1, tune_value(IM_TUNE_RG_EVALS)));
     a.stats = p->rg_stats;
     a.mask = use_masks ? (unsigned long long *)(Bs + o_mask) : nullptr;
     a.gbuf = use_masks ? (uint32_t *)(Bs + o_gbuf) : nullptr;

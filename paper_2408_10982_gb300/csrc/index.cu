@@ -20,34 +20,14 @@ namespace {
 
 constexpr int kChunk = 4096;   // vertices per chunk of the stable partition scatter
 
-// Each warp takes 32 consecutive sets and spreads their members over lanes.
-template <typename F>
-__device__ __forceinline__ void for_each_entry_of_32_sets(const int64_t *set_off, int64_t i0,
-                                                          int64_t theta, int lane, F &&f) {
-    const int64_t i = i0 + lane;
-    int64_t o = 0, len = 0;
-    if (i < theta) {
-        o = set_off[i];
-        len = set_off[i + 1] - o;
-    }
-    const int64_t incl = warp_incl_scan<int64_t>(len, lane);
-    const int64_t total = __shfl_sync(kFull, incl, 31);
-    for (int64_t base = 0; base < total; base += 32) {
-        const int64_t t = base + lane;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
-            if (c <= t) owner += step;
-        }
-        const int64_t o_incl = __shfl_sync(kFull, incl, owner);
-        const int64_t o_len = __shfl_sync(kFull, len, owner);
-        const int64_t o_off = __shfl_sync(kFull, o, owner);
-        if (t < total) f(i0 + owner, o_off + (t - (o_incl - o_len)));
-    }
-}
+// Counters are replicated R times (replica of member position t: (t >> 12) % R,
+// the same rule in the histogram and the scatter) so that the atomics on a
+// hub vertex, which appears in a large share of the sets, spread over R
+// addresses instead of queueing on one.
+__device__ __forceinline__ int64_t replica_of(int64_t t, int32_t R) { return (t >> 12) % R; }
 
-__global__ void k_vertex_hist(const int32_t *members, int64_t T, int32_t *cnt) {
+__global__ void k_vertex_hist(const int32_t *members, int64_t T, int32_t *cnt, int64_t n,
+                              int32_t R) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < T;
@@ -55,21 +35,65 @@ __global__ void k_vertex_hist(const int32_t *members, int64_t T, int32_t *cnt) {
         const int64_t t = base + lane;
         const int32_t u = t < T ? members[t] : -1 - lane;   // distinct dummies
         const unsigned peers = __match_any_sync(kFull, u);
-        if (u >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[u], __popc(peers));
+        if (u >= 0 && lane == __ffs(peers) - 1)
+            atomicAdd(&cnt[replica_of(t, R) * n + u], __popc(peers));
+    }
+}
+
+// total[v] = sum of v's replica counts; each replica count becomes the
+// replica's starting offset inside S(v)
+__global__ void k_replica_offsets(int32_t *cnt, int64_t n, int32_t R, int32_t *total) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = 0;
+        for (int32_t r = 0; r < R; ++r) {
+            const int32_t x = cnt[r * n + v];
+            cnt[r * n + v] = c;
+            c += x;
+        }
+        total[v] = c;
     }
 }
 
 __global__ void k_scatter(const int64_t *set_off, const int32_t *members, int64_t theta,
-                          const int64_t *vtx_off, int32_t *cursor, int32_t *set_ids) {
+                          const int64_t *vtx_off, int32_t *cursor, int64_t n, int32_t R,
+                          int32_t *set_ids) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
          i0 < theta; i0 += warps * 32) {
-        for_each_entry_of_32_sets(set_off, i0, theta, lane, [&](int64_t i, int64_t t) {
-            const int32_t u = members[t];
-            const int64_t pos = vtx_off[u] + atomicAdd(&cursor[u], 1);
-            set_ids[pos] = (int32_t)i;
-        });
+        // the 32 sets' members are contiguous from set_off[i0]; the lane of a
+        // position is found among the inclusive set sizes, U positions per
+        // lane at a time so that U cursor atomics are in flight
+        const int64_t i = i0 + lane;
+        int64_t len = 0;
+        if (i < theta) len = set_off[i + 1] - set_off[i];
+        const int64_t incl = warp_incl_scan<int64_t>(len, lane);
+        const int64_t total = __shfl_sync(kFull, incl, 31);
+        const int64_t first = set_off[i0];
+        constexpr int U = 4;
+        for (int64_t base = 0; base < total; base += 32 * U) {
+            int32_t sid[U], u[U];
+            int64_t t[U], pos[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                t[q] = base + q * 32 + lane;
+                int owner = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
+                    if (c <= t[q]) owner += step;
+                }
+                sid[q] = (int32_t)(i0 + owner);
+                u[q] = t[q] < total ? __ldg(members + first + t[q]) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q)
+                pos[q] = u[q] >= 0 ? atomicAdd(&cursor[replica_of(first + t[q], R) * n + u[q]], 1) : 0;
+#pragma unroll
+            for (int q = 0; q < U; ++q)
+                if (u[q] >= 0) set_ids[vtx_off[u[q]] + pos[q]] = sid[q];
+        }
     }
 }
 
@@ -178,20 +202,31 @@ im_status launch_partition_labels(int64_t n, int32_t P, uint64_t pseed, int32_t 
 }
 
 im_status build_index_raw(const int64_t *set_off, const int32_t *members, int64_t theta, int64_t T,
-                          int64_t n, int64_t *vtx_off, int32_t *set_ids, int32_t *cursor, void *tmp,
-                          cudaStream_t st) {
-    IM_CUDA(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), st));
+                          int64_t n, int64_t *vtx_off, int32_t *set_ids, int32_t *cursor,
+                          int32_t replicas, void *tmp, cudaStream_t st) {
+    // cursor holds R counter replicas and, when R > 1, a row of totals
+    const int32_t R = std::max<int32_t>(1, replicas);
+    const size_t rows = (size_t)R * n;
+    IM_CUDA(cudaMemsetAsync(cursor, 0, rows * sizeof(int32_t), st));
     if (T > 0) {
         KernelTimer kt(st, "index_hist");
-        k_vertex_hist<<<num_sms() * 8, 256, 0, st>>>(members, T, cursor);
+        k_vertex_hist<<<num_sms() * 8, 256, 0, st>>>(members, T, cursor, n, R);
     }
     IM_CUDA(cudaGetLastError());
-    im_status s = exclusive_scan_i32_to_i64(cursor, vtx_off, n, nullptr, tmp, scan_tmp_bytes(n), st);
+    int32_t *total = cursor;
+    if (R > 1) {
+        total = cursor + rows;
+        KernelTimer kt(st, "index_hist");
+        k_replica_offsets<<<num_sms() * 4, 256, 0, st>>>(cursor, n, R, total);
+    }
+    IM_CUDA(cudaGetLastError());
+    im_status s = exclusive_scan_i32_to_i64(total, vtx_off, n, nullptr, tmp, scan_tmp_bytes(n), st);
     if (s != IM_OK) return s;
-    IM_CUDA(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), st));
+    if (R == 1) IM_CUDA(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), st));
     if (theta > 0) {
         KernelTimer kt(st, "index_scatter");
-        k_scatter<<<num_sms() * 8, 256, 0, st>>>(set_off, members, theta, vtx_off, cursor, set_ids);
+        k_scatter<<<num_sms() * 8, 256, 0, st>>>(set_off, members, theta, vtx_off, cursor, n, R,
+                                                 set_ids);
     }
     IM_CUDA(cudaGetLastError());
     return IM_OK;
@@ -203,7 +238,7 @@ im_status build_index(im_pool *p, cudaStream_t st) {
     im_status s = pool_scratch(p, scan_tmp_bytes(p->g->n), &tmp);
     if (s != IM_OK) return s;
     s = build_index_raw(p->set_off, p->members, p->theta, p->total, p->g->n, p->vtx_off, p->set_ids,
-                        p->vtx_cursor, tmp, st);
+                        p->vtx_cursor, (int32_t)tune_value(IM_TUNE_INDEX_REPLICAS), tmp, st);
     if (s != IM_OK) return s;
     p->index_valid = true;
     return IM_OK;

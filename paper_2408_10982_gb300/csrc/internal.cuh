@@ -259,6 +259,7 @@ class KernelTimer {
 
 // process-wide tuning knobs (im_tune_set); results never depend on them
 int64_t tune_value(int32_t knob);
+constexpr int32_t kMaxIndexReplicas = 8;   // largest IM_TUNE_INDEX_REPLICAS value
 
 // scratch arena of a pool: returns a pointer to at least `bytes` (256-aligned)
 im_status pool_scratch(im_pool *p, size_t bytes, void **out);
@@ -308,8 +309,8 @@ im_status build_lt_index(im_graph *g, cudaStream_t st);
 // index.cu
 im_status build_index(im_pool *p, cudaStream_t st);
 im_status build_index_raw(const int64_t *set_off, const int32_t *members, int64_t theta, int64_t T,
-                          int64_t n, int64_t *vtx_off, int32_t *set_ids, int32_t *cursor, void *tmp,
-                          cudaStream_t st);
+                          int64_t n, int64_t *vtx_off, int32_t *set_ids, int32_t *cursor,
+                          int32_t replicas, void *tmp, cudaStream_t st);
 im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st);
 im_status launch_partition_labels(int64_t n, int32_t P, uint64_t pseed, int32_t *part,
                                   cudaStream_t st);

@@ -390,6 +390,8 @@ def im_pool_sample_bytes(p) -> int:
 
 IM_TUNE_LT_GROUP = 0
 IM_TUNE_RG_CLUSTER = 1
+IM_TUNE_INDEX_REPLICAS = 2
+IM_TUNE_RG_EVALS = 3
 
 
 def im_tune_set(knob: int, value: int):

@@ -361,3 +361,35 @@ def test_server_results_equal_alone(im):
             im.im_server_poll(srv, 10**9, 4)      # unknown (or already collected) ticket
     finally:
         im.im_server_destroy(srv)
+
+
+@pytest.mark.parametrize("replicas", [1, 2, 4, 8])
+def test_index_replicas_identical(im, replicas):
+    """Replicated counters in the covering-subset build (a tuning knob) give
+    the same covering subsets (as sorted lists) and the same greedy result."""
+    old = im.im_tune_get(im.IM_TUNE_INDEX_REPLICAS)
+    im.im_tune_set(im.IM_TUNE_INDEX_REPLICAS, replicas)
+    try:
+        g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+        G, P = gpu_pool(im, g, im.IM_LT, 42, [(0, 40000)])
+        ref = O.sample(O.LT, g, 42, 0, 40000)
+        assert_index_equal(P, g, ref)
+        c = P.cover(30)
+        rc = O.greedy(g.n, ref, O.invert(g.n, ref), 30)
+        assert c.seeds.tolist() == rc.seeds.tolist() and c.coverage == rc.coverage
+    finally:
+        im.im_tune_set(im.IM_TUNE_INDEX_REPLICAS, old)
+
+
+@pytest.mark.parametrize("evals", [1, 2, 4, 8])
+def test_randgreedi_eval_width_identical(im, evals):
+    """Candidates re-evaluated per round in the local greedy (a tuning knob):
+    every local solution and bucket stays the oracle's."""
+    old = im.im_tune_get(im.IM_TUNE_RG_EVALS)
+    im.im_tune_set(im.IM_TUNE_RG_EVALS, evals)
+    try:
+        g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+        _rg_compare(im, g, im.IM_LT, 30000, 60, 148, (1, 4), 0.077, False)
+        _rg_compare(im, g, im.IM_LT, 30000, 20, 7, (1, 1), 0.077, True)
+    finally:
+        im.im_tune_set(im.IM_TUNE_RG_EVALS, old)
