@@ -529,7 +529,7 @@ def bench_served(im, torch, orkut: bool):
     graphs, G = _batched_graphs(im)
     if any(q.graph == "orkut" for q in specs):
         G["orkut"] = im.Graph(inputs.graph_orkut_like(SEED))
-    srv = im.im_server_create(workers=2, max_batch=64, mem_budget=96 << 30)
+    srv = im.im_server_create(workers=2, max_batch=8, mem_budget=96 << 30)
     warm = [im.im_server_submit(srv, G[q.graph].handle, q.model, q.k, q.theta, q.seed)
             for q in specs[:16]]
     for t in warm:
@@ -567,6 +567,7 @@ def bench_served(im, torch, orkut: bool):
     for g in G.values():
         g.close()
     return {"workload": f"{nq} Poisson arrivals at 200/s from the batched mix"
+                        + " (im_server: 2 workers, batches of up to 8)"
                         + (", 5% Orkut-shaped (IC p=0.01, theta in [2^6,2^10])" if orkut else ""),
             "queries": nq, "span_s": round(specs[-1].arrival_s, 3),
             "q_per_s": round(nq / t_all, 2), "p50_ms": round(float(np.percentile(lat, 50)), 2),

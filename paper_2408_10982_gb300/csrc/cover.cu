@@ -127,6 +127,9 @@ struct GreedyArgs {
     int32_t *nseeds;
     int64_t *coverage;
     int *status;
+    // a query inside a batch: set ids in set_ids and vertex ids in members are
+    // offset by sshift and vshift (the query's first set and first vertex)
+    int64_t sshift, vshift;
 };
 
 __global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
@@ -176,8 +179,9 @@ __global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
             bool fresh = false;
             if (t < se) {
                 i = a.set_ids[t];
-                const uint32_t bit = 1u << (i & 31);
-                fresh = !(atomicOr(&a.covered[i >> 5], bit) & bit);
+                const int64_t il = i - a.sshift;
+                const uint32_t bit = 1u << (il & 31);
+                fresh = !(atomicOr(&a.covered[il >> 5], bit) & bit);
             }
             if (!__any_sync(kFull, fresh)) continue;
             // decrement the gains of every member of the lane's newly covered
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
                 }
 #pragma unroll
                 for (int uu = 0; uu < U; ++uu)
-                    if (mv[uu] >= 0) atomicSub(&a.counts[mv[uu]], 1);
+                    if (mv[uu] >= 0) atomicSub(&a.counts[mv[uu] - a.vshift], 1);
             }
         }
         if (!grid_sync(a.bar, nb, a.status)) return;
@@ -1078,6 +1082,8 @@ im_status greedy_plain(im_pool *p, int32_t k, int32_t *d_seeds, int64_t *d_gains
     a.nseeds = d_nseeds;
     a.coverage = d_cov;
     a.status = d_status;
+    a.sshift = 0;
+    a.vshift = 0;
     void *args[] = {&a};
     KernelTimer kt(st, "greedy");
     IM_CUDA(cudaLaunchCooperativeKernel((const void *)k_greedy, dim3(grid), dim3(kGreedyThreads),
@@ -1092,6 +1098,20 @@ im_status greedy_launch(int64_t n, int64_t theta, const int64_t *set_off, const 
                         uint32_t *covered, unsigned long long *block_best, int max_grid,
                         void *barrier, int32_t *seeds, int64_t *gains, int32_t *nseeds,
                         int64_t *coverage, int *status, cudaStream_t st) {
+    return greedy_launch_view(n, theta, set_off, members, vtx_off, set_ids, 0, 0, k, counts,
+                              covered, block_best, max_grid, barrier, seeds, gains, nseeds,
+                              coverage, status, st);
+}
+
+// The same over one query of a batch: vtx_off points at the query's first
+// vertex, set_ids / members hold batch-wide set and vertex ids, offset by
+// sshift and vshift from the query's own.
+im_status greedy_launch_view(int64_t n, int64_t theta, const int64_t *set_off,
+                             const int32_t *members, const int64_t *vtx_off,
+                             const int32_t *set_ids, int64_t sshift, int64_t vshift, int32_t k,
+                             int32_t *counts, uint32_t *covered, unsigned long long *block_best,
+                             int max_grid, void *barrier, int32_t *seeds, int64_t *gains,
+                             int32_t *nseeds, int64_t *coverage, int *status, cudaStream_t st) {
     int per_sm = 0;
     IM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy, kGreedyThreads, 0));
     if (per_sm < 1) return IM_ERR_UNSUPPORTED;
@@ -1113,6 +1133,8 @@ im_status greedy_launch(int64_t n, int64_t theta, const int64_t *set_off, const 
     a.nseeds = nseeds;
     a.coverage = coverage;
     a.status = status;
+    a.sshift = sshift;
+    a.vshift = vshift;
     void *args[] = {&a};
     KernelTimer kt(st, "greedy");
     IM_CUDA(cudaLaunchCooperativeKernel((const void *)k_greedy, dim3(grid), dim3(kGreedyThreads),

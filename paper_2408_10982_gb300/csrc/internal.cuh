@@ -325,6 +325,12 @@ im_status greedy_launch(int64_t n, int64_t theta, const int64_t *set_off, const 
                         uint32_t *covered, unsigned long long *block_best, int max_grid,
                         void *barrier, int32_t *seeds, int64_t *gains, int32_t *nseeds,
                         int64_t *coverage, int *status, cudaStream_t st);
+im_status greedy_launch_view(int64_t n, int64_t theta, const int64_t *set_off,
+                             const int32_t *members, const int64_t *vtx_off,
+                             const int32_t *set_ids, int64_t sshift, int64_t vshift, int32_t k,
+                             int32_t *counts, uint32_t *covered, unsigned long long *block_best,
+                             int max_grid, void *barrier, int32_t *seeds, int64_t *gains,
+                             int32_t *nseeds, int64_t *coverage, int *status, cudaStream_t st);
 im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_seeds,
                      int64_t *d_gains, int32_t *d_nseeds, int64_t *d_cov, cudaStream_t st,
                      int *d_status);

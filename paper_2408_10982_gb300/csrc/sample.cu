@@ -27,6 +27,7 @@ constexpr int kPathSmem = 256;               // LT path entries mirrored in smem
 constexpr int kPathSmemGroup = 64;           // ... per walk when a warp runs several walks
 constexpr int64_t kQueueCapIC = 1 << 14;     // per-warp queue entries (first pass)
 constexpr int64_t kQueueCapLT = 1 << 11;
+constexpr int kICU = 2;                      // IC edge groups per lane in flight
 constexpr int kWarpSortBytes = 4096;         // per-warp smem sort buffer
 constexpr int kBlockSortCap = 16384;         // ... by one block in shared memory (int32)
 
@@ -152,39 +153,57 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
             const int64_t ng = ee > eb ? ((ee - 1) >> 2) - g0 + 1 : 0;
             const int64_t incl = warp_incl_scan<int64_t>(ng, lane);
             const int64_t total = __shfl_sync(kFull, incl, 31);
-            for (int64_t base = 0; base < total; base += 32) {
-                const int64_t t = base + lane;
-                int owner = 0;   // first lane whose inclusive group count exceeds t
+            // kICU edge groups per lane per iteration: their loads and coin
+            // draws are independent, so they overlap
+            for (int64_t base = 0; base < total; base += 32 * kICU) {
+                uint4 wv[kICU];
+                int4 sv[kICU];
+                int64_t gg[kICU], lo[kICU], hi[kICU];
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
-                    if (c <= t) owner += step;
+                for (int uu = 0; uu < kICU; ++uu) {
+                    const int64_t t = base + uu * 32 + lane;
+                    int owner = 0;   // first lane whose inclusive group count exceeds t
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
+                        if (c <= t) owner += step;
+                    }
+                    const int64_t o_incl = __shfl_sync(kFull, incl, owner);
+                    const int64_t o_ng = __shfl_sync(kFull, ng, owner);
+                    const int64_t o_g0 = __shfl_sync(kFull, g0, owner);
+                    lo[uu] = __shfl_sync(kFull, eb, owner);
+                    hi[uu] = __shfl_sync(kFull, ee, owner);
+                    gg[uu] = -1;
+                    if (t < total) {
+                        gg[uu] = o_g0 + (t - (o_incl - o_ng));
+                        wv[uu] = __ldg(reinterpret_cast<const uint4 *>(wgt) + gg[uu]);
+                        sv[uu] = __ldg(reinterpret_cast<const int4 *>(in_src) + gg[uu]);
+                    }
                 }
-                const int64_t o_incl = __shfl_sync(kFull, incl, owner);
-                const int64_t o_ng = __shfl_sync(kFull, ng, owner);
-                const int64_t o_g0 = __shfl_sync(kFull, g0, owner);
-                const int64_t o_eb = __shfl_sync(kFull, eb, owner);
-                const int64_t o_ee = __shfl_sync(kFull, ee, owner);
                 unsigned fresh = 0;
-                int32_t src[4] = {0, 0, 0, 0};
-                if (t < total) {
-                    const int64_t g = o_g0 + (t - (o_incl - o_ng));
+                int32_t src[4 * kICU];
+#pragma unroll
+                for (int uu = 0; uu < kICU; ++uu) {
+                    src[4 * uu + 0] = src[4 * uu + 1] = src[4 * uu + 2] = src[4 * uu + 3] = 0;
+                    if (gg[uu] < 0) continue;
+                    const int64_t g = gg[uu];
                     const uint4 coin = philox4x32_10(
                         make_uint4(s, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), kStreamCoin), k0,
                         k1);
-                    const uint4 wv = __ldg(reinterpret_cast<const uint4 *>(wgt) + g);
-                    const int4 sv = __ldg(reinterpret_cast<const int4 *>(in_src) + g);
                     const uint32_t cv[4] = {coin.x, coin.y, coin.z, coin.w};
-                    const uint32_t wq[4] = {wv.x, wv.y, wv.z, wv.w};
-                    src[0] = sv.x; src[1] = sv.y; src[2] = sv.z; src[3] = sv.w;
+                    const uint32_t wq[4] = {wv[uu].x, wv[uu].y, wv[uu].z, wv[uu].w};
+                    src[4 * uu + 0] = sv[uu].x;
+                    src[4 * uu + 1] = sv[uu].y;
+                    src[4 * uu + 2] = sv[uu].z;
+                    src[4 * uu + 3] = sv[uu].w;
                     const int64_t e0 = g << 2;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const int64_t e = e0 + c;
-                        if (e >= o_eb && e < o_ee && cv[c] < wq[c]) {
-                            const uint32_t u = (uint32_t)src[c];
+                        if (e >= lo[uu] && e < hi[uu] && cv[c] < wq[c]) {
+                            const uint32_t u = (uint32_t)src[4 * uu + c];
                             const uint32_t bit = 1u << (u & 31);
-                            if (!(atomicOr(&vis[u >> 5], bit) & bit)) fresh |= 1u << c;
+                            if (!(atomicOr(&vis[u >> 5], bit) & bit)) fresh |= 1u << (4 * uu + c);
                         }
                     }
                 }
@@ -195,7 +214,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
                 if (tail + totf > a.qcap) {
                     // drop this sample; un-mark what was just marked
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
+                    for (int c = 0; c < 4 * kICU; ++c)
                         if (fresh >> c & 1) {
                             const uint32_t u = (uint32_t)src[c];
                             atomicAnd(&vis[u >> 5], ~(1u << (u & 31)));
@@ -205,7 +224,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
                 }
                 int64_t pos = tail + inclf - nf;
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
+                for (int c = 0; c < 4 * kICU; ++c)
                     if (fresh >> c & 1) q[pos++] = src[c];
                 tail += totf;
                 __syncwarp();
