@@ -122,3 +122,57 @@ def covering_subsets(n: int, sets: list) -> list[set]:
         for v in r:
             out[int(v)].add(i)
     return out
+
+
+def _forward_reach(n, in_off, in_src, live, seeds):
+    out = [[] for _ in range(n)]
+    for v in range(n):
+        for e in range(int(in_off[v]), int(in_off[v + 1])):
+            if live[e]:
+                out[int(in_src[e])].append(v)
+    seen = set(int(s) for s in seeds)
+    stack = list(seen)
+    while stack:
+        u = stack.pop()
+        for v in out[u]:
+            if v not in seen:
+                seen.add(v)
+                stack.append(v)
+    return seen
+
+
+def ic_spread_exact(graph, seeds) -> Fraction:
+    """sigma(S) = E |vertices reachable from S| over every IC live-edge world."""
+    m = graph.m
+    p = [Fraction(int(x), TWO32) for x in graph.w]
+    total = Fraction(0)
+    for mask in range(1 << m):
+        live = [(mask >> e) & 1 for e in range(m)]
+        prob = Fraction(1)
+        for e in range(m):
+            prob *= p[e] if live[e] else 1 - p[e]
+        if prob:
+            total += prob * len(_forward_reach(graph.n, graph.in_off, graph.in_src, live, seeds))
+    return total
+
+
+def lt_spread_exact(graph, seeds) -> Fraction:
+    """sigma(S) under LT: each vertex keeps at most one in-edge (w / 2^32 each)."""
+    n, m = graph.n, graph.m
+    options = []
+    for v in range(n):
+        b, e = int(graph.in_off[v]), int(graph.in_off[v + 1])
+        opts = [(None, Fraction(TWO32 - sum(int(graph.w[x]) for x in range(b, e)), TWO32))]
+        opts += [(x, Fraction(int(graph.w[x]), TWO32)) for x in range(b, e)]
+        options.append(opts)
+    total = Fraction(0)
+    for choice in itertools.product(*options):
+        prob = Fraction(1)
+        live = [0] * m
+        for e, pr in choice:
+            prob *= pr
+            if e is not None:
+                live[e] = 1
+        if prob:
+            total += prob * len(_forward_reach(n, graph.in_off, graph.in_src, live, seeds))
+    return total

@@ -402,6 +402,78 @@ int orc_randgreedi(int64_t n, int64_t theta, const int64_t *set_off, const int32
 }
 
 /* ------------------------------------------------------------------------ */
+/* Forward simulation of the diffusion from a seed set: the expected number */
+/* of vertices the seeds activate, sigma(S), is what the selected seeds are */
+/* judged by (Sec. 2, Def. of influence spread; Sec. 4.1 reports it).  Run */
+/* r uses the live-edge world of sample id r -- the IC coins and LT picks */
+/* of RRR sample r -- and activates every vertex reachable from S over live */
+/* edges (BFS over out-edges).  IC: in-edge e is live iff its coin < w[e]. */
+/* LT: in-edge e of v is live iff it is v's pick, found by scanning v's     */
+/* in-edges with the running weight sum.                                    */
+/* Outputs per run: activated[i] = |Reach(S)|, root_hit[i] = 1 if the root */
+/* of sample r is activated -- by the RIS identity, exactly when S meets    */
+/* RRR set r.                                                               */
+/* ------------------------------------------------------------------------ */
+static int64_t lt_pick(const int64_t *in_off, const uint32_t *w, uint64_t seed, uint32_t s,
+                       uint32_t v) {
+    uint32_t x = orc_lt_draw(seed, s, v);
+    uint64_t c = 0;
+    for (int64_t e = in_off[v]; e < in_off[v + 1]; ++e) {
+        c += w[e];
+        if ((uint64_t)x < c) return e;
+    }
+    return -1;
+}
+
+int orc_spread(int model, int64_t n, const int64_t *in_off, const int32_t *in_src,
+               const uint32_t *w, uint64_t seed, uint64_t first, uint64_t runs,
+               const int32_t *seeds, int32_t k, int64_t *activated, uint8_t *root_hit) {
+    int64_t m = in_off[n];
+    int32_t *dst = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    int64_t *out_off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t *out_e = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+    int64_t *fill = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    uint8_t *visited = (uint8_t *)calloc((size_t)n, 1);
+    int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!dst || !out_off || !out_e || !fill || !visited || !queue) {
+        free(dst); free(out_off); free(out_e); free(fill); free(visited); free(queue);
+        return -1;
+    }
+    /* head of every in-edge, and the out-edges of every vertex (in-CSR ids) */
+    for (int64_t v = 0; v < n; ++v)
+        for (int64_t e = in_off[v]; e < in_off[v + 1]; ++e) dst[e] = (int32_t)v;
+    for (int64_t e = 0; e < m; ++e) out_off[in_src[e] + 1]++;
+    for (int64_t v = 0; v < n; ++v) out_off[v + 1] += out_off[v];
+    for (int64_t v = 0; v < n; ++v) fill[v] = out_off[v];
+    for (int64_t e = 0; e < m; ++e) out_e[fill[in_src[e]]++] = e;
+
+    for (uint64_t i = 0; i < runs; ++i) {
+        uint32_t s = (uint32_t)(first + i);
+        int64_t tail = 0;
+        for (int32_t j = 0; j < k; ++j) {
+            int32_t u = seeds[j];
+            if (!visited[u]) { visited[u] = 1; queue[tail++] = u; }
+        }
+        for (int64_t head = 0; head < tail; ++head) {
+            int32_t u = queue[head];
+            for (int64_t t = out_off[u]; t < out_off[u + 1]; ++t) {
+                int64_t e = out_e[t];
+                int32_t v = dst[e];
+                if (visited[v]) continue;
+                int live = model == 0 ? orc_ic_coin(seed, s, e) < w[e]
+                                      : lt_pick(in_off, w, seed, s, (uint32_t)v) == e;
+                if (live) { visited[v] = 1; queue[tail++] = v; }
+            }
+        }
+        activated[i] = tail;
+        if (root_hit) root_hit[i] = visited[orc_root(seed, s, n)];
+        for (int64_t t = 0; t < tail; ++t) visited[queue[t]] = 0;
+    }
+    free(dst); free(out_off); free(out_e); free(fill); free(visited); free(queue);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* IMM sampling-effort formulas.  Alg. 1 (Sec. 2.1) names Estimate,          */
 /* CheckGoodness and theta = f(LB) but defers their values to Tang et al.    */
 /* (SIGMOD 2015) and Chen (2018); they are written out here from that work,  */

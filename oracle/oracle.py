@@ -77,6 +77,8 @@ def _lib():
         lib.orc_bucket_thresholds.argtypes = [i64, i32, ctypes.c_double, i32, vp]
         lib.orc_stream_buckets.restype = ctypes.c_int
         lib.orc_stream_buckets.argtypes = [i64, vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
+        lib.orc_spread.restype = ctypes.c_int
+        lib.orc_spread.argtypes = [ctypes.c_int, i64, vp, vp, vp, u64, u64, u64, vp, i32, vp, vp]
         lib.orc_randgreedi.restype = ctypes.c_int
         lib.orc_randgreedi.argtypes = [i64, i64, vp, vp, vp, vp, i32, i32, u64, i32,
                                        ctypes.c_double] + [vp] * 14
@@ -298,3 +300,23 @@ def ratio_streaming(eps: float, delta: float) -> float:
 def ratio_truncated_streaming(alpha: float, eps: float, delta: float) -> float:
     """Lemma 3: truncated locals (1-e^-alpha) with (1/2-delta) streaming, minus eps."""
     return ratio_randgreedi(1.0 - np.exp(-alpha), 0.5 - delta) - eps
+
+
+# --- forward simulation -------------------------------------------------------
+
+def spread(model: int, graph, seed: int, first: int, runs: int, seeds) -> tuple[np.ndarray, np.ndarray]:
+    """Forward simulation from `seeds` in the live-edge worlds of sample ids
+    first .. first+runs-1: (activated int64[runs], root_hit uint8[runs])."""
+    if first + runs > 1 << 32:
+        raise ValueError("run ids must stay below 2^32")
+    in_off = _c(graph.in_off, np.int64)
+    in_src = _c(graph.in_src, np.int32)
+    w = _c(graph.w, np.uint32)
+    sd = _c(seeds, np.int32)
+    act = np.zeros(runs, np.int64)
+    hit = np.zeros(runs, np.uint8)
+    rc = _lib().orc_spread(model, graph.n, _p(in_off), _p(in_src), _p(w), seed, first, runs,
+                           _p(sd), len(sd), _p(act), _p(hit))
+    if rc != 0:
+        raise MemoryError("oracle spread ran out of memory")
+    return act, hit
