@@ -312,6 +312,7 @@ def run_ours(args):
             "gpu_launches": launches, "roofline": roofline, "clocks": clk}
 
     pool_stats = cover_stats(im, pool, g.n, theta, K, opts_rg)
+    spread = bench_spread(im, torch, G, pool, g.n, theta) if not args.no_extras else None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["bit_exact"], line["cpu_baseline"] = cpu_baseline_and_check(g, pool, first)
     if not args.no_e2e:
@@ -319,6 +320,8 @@ def run_ours(args):
     pool.close()
     G.close()
     line["kernels"] = kernel_rooflines(im, pool_stats, per, hbm)
+    if spread:
+        line["spread"] = spread
     if not args.no_extras:
         line["batched"] = bench_batched(im, torch)
         line["served"] = bench_served(im, torch, args.served_orkut)
@@ -578,6 +581,30 @@ def bench_served(im, torch, orkut: bool):
             "plain_p99_ms": round(float(np.percentile(plat, 99)), 2),
             "plain_busy_s": round(float(sum(service)), 3),
             "bit_exact_vs_plain": bool(same)}
+
+
+def bench_spread(im, torch, G, pool, n, theta):
+    """Quality of the plain greedy's seeds: forward simulation of 1,024 runs
+    in fresh live-edge worlds (sample ids from 2^30) against the RIS estimate
+    n * coverage / theta of the pool they were selected on."""
+    c = pool.cover(K)
+    runs = 1024
+    act = np.zeros(runs, np.int64)
+    im.im_spread(G.handle, im.IM_LT, c.seeds, SEED, 1 << 30, 64, None, None)   # warm-up
+    torch.cuda.synchronize()
+    im.im_profile_reset()
+    im.im_profile_enable(True)
+    t0 = time.perf_counter()
+    tot = im.im_spread(G.handle, im.IM_LT, c.seeds, SEED, 1 << 30, runs, act, None)
+    dt = time.perf_counter() - t0
+    im.im_profile_enable(False)
+    k_ms = im.im_profile_read().get("spread_lt", (1, 0.0))[1]
+    mean = tot / runs
+    return {"workload": f"LT forward simulation of the plain greedy's {K} seeds on rmat20-lt, "
+                        f"{runs} runs (sample ids from 2^30)",
+            "sigma_mc": round(mean, 1), "sigma_mc_stderr": round(float(act.std() / np.sqrt(runs)), 1),
+            "sigma_ris": round(n * c.coverage / theta, 1), "ms": round(1000 * dt, 2),
+            "kernel_ms": round(k_ms, 2), "activations_per_s": tot / dt}
 
 
 def bench_imm(im, torch, g):

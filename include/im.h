@@ -352,6 +352,27 @@ im_status im_server_wait(im_server *s, uint64_t ticket, double timeout_s, int32_
 /* Batches run, requests they held, requests still queued. */
 im_status im_server_stats(im_server *s, int64_t *batches, int64_t *queries, int64_t *queued);
 
+/* ---- spread of a seed set by forward simulation (Sec. 2; Sec. 4.1) ---------------
+ * The influence spread sigma(S) is the expected number of vertices S activates.
+ * Run r (r = first_run .. first_run + runs - 1) simulates the live-edge world of
+ * RRR sample r -- the IC coins and LT picks im_sample_rrr uses for sample id r
+ * under the same seed -- forward from S and counts the activated vertices.
+ *   seeds      int32[k], host or device; duplicates allowed; ids in [0, n)
+ *              (IM_ERR_INVALID_ARG otherwise)
+ *   activated  int64[runs] (host or device, may be NULL): |activated set| of each run
+ *   root_hit   uint8[runs] (host or device, may be NULL): 1 iff the run's root (the
+ *              root of RRR sample r) is activated -- by the RIS identity, iff S
+ *              meets RRR set r, so sum(root_hit) over runs 0 .. theta-1 equals the
+ *              coverage of S on a pool of those samples
+ *   total      host int64 (may be NULL): sum of activated; total / runs estimates
+ *              sigma(S)
+ * LT requires lt_valid.  Builds the graph's out-edge index on first use (kept
+ * with the graph).  Device scratch is allocated stream-ordered per call.
+ * Synchronises the stream. */
+im_status im_spread(const im_graph *g, im_model model, const int32_t *seeds, int32_t k,
+                    uint64_t seed, uint64_t first_run, uint64_t runs, int64_t *activated,
+                    uint8_t *root_hit, int64_t *total, void *stream);
+
 /* Vertex partition of Alg. 3: part[v] = (Philox(v,0,0,4).x * P) >> 32. */
 im_status im_partition(int64_t n, int32_t P, uint64_t partition_seed, int32_t *part,
                        void *stream);

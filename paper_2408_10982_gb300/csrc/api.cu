@@ -137,28 +137,6 @@ im_status pool_scratch(im_pool *p, size_t bytes, void **out) {
 
 namespace {
 
-bool is_device_ptr(const void *ptr) {
-    if (!ptr) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 __global__ void k_validate_graph(const int64_t *in_off, const int32_t *in_src, int64_t n,
                                  int64_t m, int *bad) {
@@ -173,7 +151,6 @@ __global__ void k_validate_graph(const int64_t *in_off, const int32_t *in_src, i
         atomicExch(bad, 3);
 }
 
-cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // copy to a caller buffer (host or device); returns whether it was host memory
 im_status copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st, bool *host) {
@@ -198,11 +175,6 @@ im_status pool_results(im_pool *p, size_t bytes, void **out) {
     return IM_OK;
 }
 
-#define IM_TRY(expr)                   \
-    do {                               \
-        im_status _s = (expr);         \
-        if (_s != IM_OK) return _s;    \
-    } while (0)
 
 }  // namespace
 }  // namespace im
@@ -313,6 +285,8 @@ im_status im_graph_destroy(im_graph *g) {
     cudaFree(g->lt_leaf);
     cudaFree(g->lt_tree);
     cudaFree(g->lt_guide);
+    cudaFree(g->out_off);
+    cudaFree(g->out_rec);
     delete g;
     return IM_OK;
 }

@@ -182,6 +182,10 @@ struct im_graph {
     unsigned long long *lt_leaf;     // [m]
     unsigned long long *lt_tree;     // [sum over vertices of the upper-level sizes]
     uint4 *lt_guide;                 // [m] inverse-CDF cut points (see k_lt_guide)
+    // out-edge index, built on first im_spread: per source, the in-CSR ids
+    // of its out-edges and their heads
+    int64_t *out_off;                // [n+1]
+    uint4 *out_rec;                  // [m] {head, in-CSR id, weight, LT interval start}
     int32_t lt_valid;
     int64_t max_indeg;
 };
@@ -240,6 +244,39 @@ im_status cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::im::cuda_fail(_e, #call);  \
     } while (0)
 im_status map_dev_status(int code, const char *where);
+
+#define IM_TRY(expr)                   \
+    do {                               \
+        im_status _s = (expr);         \
+        if (_s != IM_OK) return _s;    \
+    } while (0)
+
+// Device (or managed) memory, as opposed to host memory.
+inline bool is_device_ptr(const void *ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Makes a handle's device current for the scope of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // Brackets the kernels launched in its scope with timing events when the
 // profiler is on (im_profile_enable); a no-op otherwise.

@@ -94,6 +94,7 @@ def lib():
             "im_server_wait": ([vp, ctypes.c_uint64, ctypes.c_double, vp, vp, vp, vp], ctypes.c_int),
             "im_server_stats": ([vp, vp, vp, vp], ctypes.c_int),
             "im_batch_destroy": ([vp], ctypes.c_int),
+            "im_spread": ([vp, ctypes.c_int, vp, i32, u64, u64, u64, vp, vp, vp, vp], ctypes.c_int),
             "im_solve_batch": ([vp, vp, i32, i32, vp, vp, vp, vp], ctypes.c_int),
             "im_solve": ([vp, ctypes.c_int, i32, ctypes.c_double, ctypes.c_double, u64, vp, vp,
                           vp, vp, vp, vp, vp], ctypes.c_int),
@@ -299,6 +300,20 @@ def im_solve_batch(b, queries, kmax: int, stream=None):
         out.append((seeds[q * kmax:q * kmax + m].copy(), gains[q * kmax:q * kmax + m].copy(),
                     res[q].coverage, res[q].entries))
     return out
+
+
+def im_spread(g, model: int, seeds, seed: int, first_run: int, runs: int, activated=None,
+              root_hit=None, stream=None) -> int:
+    """Forward simulation of runs first_run .. first_run+runs-1 from `seeds`
+    (host numpy / torch, host or device); fills `activated` int64[runs] and
+    `root_hit` uint8[runs] when given; returns the total activated count."""
+    sd = np.ascontiguousarray(seeds, dtype=np.int32) if isinstance(seeds, (list, tuple, np.ndarray)) \
+        else seeds
+    total = ctypes.c_int64()
+    _check(lib().im_spread(g.value if hasattr(g, "value") else g, model, _ptr(sd), len(sd), seed,
+                           first_run, runs, _ptr(activated), _ptr(root_hit), ctypes.byref(total),
+                           _stream(stream)), "im_spread")
+    return total.value
 
 
 class ServerOpts(ctypes.Structure):

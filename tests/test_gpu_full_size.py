@@ -182,3 +182,28 @@ def test_served_trace_results_equal_alone(im):
         assert seeds.tolist() == s1.tolist(), q
         assert cov == c1, q
         assert lat > 0
+
+
+def test_rmat20_lt_spread_of_greedy_seeds(im):
+    """The bench workload's plain-greedy seeds (on the first 65,536 sets): the
+    root hits of the forward runs over sample ids 0..4095 equal the seeds'
+    coverage of those sets in the oracle's pool, and two runs equal the
+    oracle's forward BFS (each run activates ~10^5 vertices)."""
+    theta, k, seed, runs = 65536, 100, 42, 4096
+    g = inputs.graph_lt_scale20(seed)
+    G = im.Graph(g)
+    pool = im.Pool(G, theta, theta * 64)
+    pool.sample(im.IM_LT, seed, 0, theta)
+    seeds = pool.cover(k).seeds
+    hit = np.zeros(runs, np.uint8)
+    im.im_spread(G.handle, im.IM_LT, seeds, seed, 0, runs, None, hit)
+    ref = O.sample(O.LT, g, seed, 0, runs)
+    S = set(int(x) for x in seeds)
+    cov = np.array([1 if S & set(int(v) for v in ref.set(i)) else 0 for i in range(runs)], np.uint8)
+    assert np.array_equal(hit, cov)
+    act = np.zeros(2, np.int64)
+    im.im_spread(G.handle, im.IM_LT, seeds, seed, 1 << 30, 2, act, None)
+    ra, _ = O.spread(O.LT, g, seed, 1 << 30, 2, seeds)
+    assert np.array_equal(act, ra)
+    pool.close()
+    G.close()

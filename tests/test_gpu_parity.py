@@ -393,3 +393,52 @@ def test_randgreedi_eval_width_identical(im, evals):
         _rg_compare(im, g, im.IM_LT, 30000, 20, 7, (1, 1), 0.077, True)
     finally:
         im.im_tune_set(im.IM_TUNE_RG_EVALS, old)
+
+
+# --- forward simulation (spread of a seed set) -----------------------------------
+
+@pytest.mark.parametrize("model,wmode", [(0, "random"), (0, "0.3"), (0, "one"), (0, "zero"),
+                                         (1, "lt"), (1, "lt_random")])
+def test_spread_matches_oracle(im, model, wmode):
+    """Per-run activated counts and root hits, bit-exact against the oracle's
+    forward BFS (duplicated seeds, ragged run counts)."""
+    g = inputs.random_graph(60, 400, 13, wmode)
+    G = im.Graph(g)
+    seeds = np.array([3, 7, 7, 41], np.int32)
+    for first, runs in ((0, 1), (5, 33), (1000, 777)):
+        act = np.zeros(runs, np.int64)
+        hit = np.zeros(runs, np.uint8)
+        tot = im.im_spread(G.handle, model, seeds, 21, first, runs, act, hit)
+        ra, rh = O.spread(model, g, 21, first, runs, seeds)
+        assert np.array_equal(act, ra) and np.array_equal(hit, rh)
+        assert tot == int(ra.sum())
+
+
+def test_spread_rmat_and_ris_identity(im):
+    """R-MAT graphs, IC and LT: the oracle's runs bit-exact, and on the device
+    the root hits of runs 0..theta-1 add up to the coverage the greedy reports
+    for its seeds on the pool of samples 0..theta-1 (two kernels, one world)."""
+    import torch
+    for model, w, theta in ((im.IM_IC, "ic0.1", 20000), (im.IM_LT, "lt", 50000)):
+        g = inputs.rmat_graph(1 << 14, 1 << 18, 42, w)
+        G = im.Graph(g)
+        P = im.Pool(G, theta, theta * 2048)
+        P.sample(model, 42, 0, theta)
+        c = P.cover(25)
+        hit = torch.zeros(theta, dtype=torch.uint8, device="cuda")
+        im.im_spread(G.handle, model, c.seeds, 42, 0, theta, None, hit)
+        assert int(hit.sum().item()) == c.coverage
+        act = np.zeros(300, np.int64)
+        rh = np.zeros(300, np.uint8)
+        im.im_spread(G.handle, model, c.seeds, 42, 777, 300, act, rh)
+        ra, rrh = O.spread(O.IC if model == im.IM_IC else O.LT, g, 42, 777, 300, c.seeds)
+        assert np.array_equal(act, ra) and np.array_equal(rh, rrh)
+
+
+def test_spread_rejects_bad_seed(im):
+    g = inputs.random_graph(30, 100, 2, "0.3")
+    G = im.Graph(g)
+    with pytest.raises(im.ImError) as e:
+        im.im_spread(G.handle, im.IM_IC, np.array([1, 30], np.int32), 1, 0, 10)
+    assert e.value.status == im.IM_ERR_INVALID_ARG
+    assert im.im_spread(G.handle, im.IM_IC, np.zeros(0, np.int32), 1, 0, 5) == 0
