@@ -92,6 +92,22 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def replica_first_id(rank: int, theta: int) -> int:
+    """Weak scaling: rank r solves its own replica over sample ids
+    [r theta, (r + 1) theta), disjoint from every other rank's."""
+    return rank * theta
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """The slowest rank's time (the job's time); x itself on one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -221,7 +237,7 @@ def run_ours(args):
     from paper_2408_10982_gb300 import build, im
     build.build_library()
     theta = args.theta
-    first = rank * theta                         # disjoint sample ids per replica
+    first = replica_first_id(rank, theta)        # disjoint sample ids per replica
     g = inputs.graph_lt_scale20(SEED)
     G = im.Graph(g)
     cap = theta * 64
@@ -267,11 +283,7 @@ def run_ours(args):
     clk = clocks.stop()
     im.im_profile_enable(False)
     prof = im.im_profile_read()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_step = elapsed_ms / args.steps
     value = world * examined / (ms_step / 1000.0)
 
@@ -381,11 +393,7 @@ def e2e(args, g, im, torch, dev, stream, first, dist):
     for _ in range(steps):
         one()
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / steps
-    if dist:
-        t = torch.tensor([dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks((time.perf_counter() - t0) / steps, dist, dev)
     world = dist.get_world_size() if dist else 1
     h2d = 8 * (g.n + 1) + 4 * g.m + 4 * g.m
     d2h = 2 * (4 * K + 8 * K + 4 + 8)
