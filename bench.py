@@ -658,13 +658,14 @@ def bench_ic(im, torch, g):
     prof = im.im_profile_read()
     _, total, examined = p.info()
     sbytes = p.sample_bytes()
-    k_ms = prof.get("sample_ic", (1, 0.0))[1]
+    k_ms = prof.get("sample_ic", (1, 0.0))[1] + prof.get("sample_ic_big", (1, 0.0))[1]
     hbm, _ = measured_peaks()
     p.close()
     G.close()
     return {"workload": "LiveJournal-shaped R-MAT (4,847,571 vertices, 69,000,000 edges), IC "
                         "trivalency, 8,192 RRR sets", "edges_per_s": examined / dt,
-            "entries": total, "ms": round(1000 * dt, 3), "kernel_ms": round(k_ms, 3),
+            "entries": total, "ms": round(1000 * dt, 3),
+            "kernel_ms": round(k_ms, 3),   # both sampling passes
             "kernel_gbs": round(sbytes / (k_ms / 1000) / 1e9, 1) if k_ms else None,
             "kernel_frac": round(sbytes / (k_ms / 1000) / 1e9 / hbm, 4) if k_ms else None,
             "phase_ms": {k: round(v[1], 3) for k, v in sorted(prof.items())}}

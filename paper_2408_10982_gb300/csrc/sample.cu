@@ -256,6 +256,174 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
     if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
 }
 
+// IC, one block per sample: the second pass for the sets longer than a warp's
+// queue.  The giant sets of hub-heavy graphs (hundreds of thousands of
+// members, tens of millions of examined in-edges) are a level-synchronous
+// BFS whose 32 warps take 32 queued vertices of the current level at a time
+// and expand their in-edges four per lane (one Philox call per group of four,
+// as in k_sample_ic), appending what they reach with one block-level atomic
+// per warp and step.  The queue and visited bitmap (n entries / n bits per
+// block) live in global memory.  The set is copied to the stage by the block.
+constexpr int kICBigThreads = 1024;
+
+// One group of four in-edges of sample s: coins, liveness, visited marks;
+// returns the fresh sources in src[] and their bits.
+__device__ __forceinline__ unsigned ic_group(const uint32_t *wgt, const int32_t *in_src, int64_t g,
+                                             int64_t eb, int64_t ee, uint32_t s, uint32_t k0,
+                                             uint32_t k1, uint32_t *vis, int32_t (&src)[4]) {
+    const uint4 wv = __ldg(reinterpret_cast<const uint4 *>(wgt) + g);
+    const int4 sv = __ldg(reinterpret_cast<const int4 *>(in_src) + g);
+    const uint4 coin = philox4x32_10(
+        make_uint4(s, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), kStreamCoin), k0, k1);
+    const uint32_t cv[4] = {coin.x, coin.y, coin.z, coin.w};
+    const uint32_t wq[4] = {wv.x, wv.y, wv.z, wv.w};
+    src[0] = sv.x;
+    src[1] = sv.y;
+    src[2] = sv.z;
+    src[3] = sv.w;
+    unsigned fresh = 0;
+    const int64_t e0 = g << 2;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int64_t e = e0 + c;
+        if (e >= eb && e < ee && cv[c] < wq[c]) {
+            const uint32_t u = (uint32_t)src[c];
+            const uint32_t bit = 1u << (u & 31);
+            if (!(atomicOr(&vis[u >> 5], bit) & bit)) fresh |= 1u << c;
+        }
+    }
+    return fresh;
+}
+
+// Appends each lane's fresh sources to the block queue (one atomic per warp).
+__device__ __forceinline__ void ic_append(unsigned fresh, const int32_t (&src)[4], int lane,
+                                          unsigned long long *tail, int32_t *q) {
+    const int nf = __popc(fresh);
+    const int inclf = warp_incl_scan<int>(nf, lane);
+    const int totf = __shfl_sync(kFull, inclf, 31);
+    if (totf == 0) return;
+    long long at = 0;
+    if (lane == 31) at = (long long)atomicAdd(tail, (unsigned long long)totf);
+    at = __shfl_sync(kFull, at, 31);
+    int64_t pos = at + inclf - nf;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (fresh >> c & 1) q[pos++] = src[c];
+}
+
+__global__ void __launch_bounds__(kICBigThreads) k_sample_ic_big(SampleArgs a) {
+    __shared__ unsigned long long s_item, s_tail, s_cursor, s_pos;
+    __shared__ unsigned long long s_red[2][kICBigThreads / 32];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *q = a.queues + (size_t)blockIdx.x * (size_t)a.qcap;
+    uint32_t *vis = a.gvis + (size_t)blockIdx.x * (size_t)a.vis_words;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(a.work, 1ull);
+            s_tail = 0;
+        }
+        __syncthreads();
+        const unsigned long long jw = s_item;
+        if (jw >= (unsigned long long)a.count) break;
+        const int64_t j = a.list ? a.list[jw] : (int64_t)jw;
+        const int qi = find_query(a, j);
+        const QueryView &V = a.qv[qi];
+        const int64_t *in_off = V.in_off;
+        const int32_t *in_src = V.in_src;
+        const uint32_t *wgt = V.w;
+        const uint32_t k0 = seed_lo(V.seed), k1 = seed_hi(V.seed);
+        const uint32_t s = V.first + (uint32_t)(j - __ldg(a.qstart + qi));
+        if (threadIdx.x == 0) {
+            const uint32_t root = rrr_root(V.seed, s, V.n);
+            atomicOr(&vis[root >> 5], 1u << (root & 31));
+            q[0] = (int32_t)root;
+            s_tail = 1;
+        }
+        __syncthreads();
+        unsigned long long sexam = 0;
+        long long head = 0;
+        for (;;) {
+            const long long lvl_end = (long long)s_tail;
+            if (head >= lvl_end) break;
+            if (threadIdx.x == 0) s_cursor = (unsigned long long)head;
+            __syncthreads();
+            for (;;) {
+                long long base = 0;
+                if (lane == 0) base = (long long)atomicAdd(&s_cursor, 32ull);
+                base = __shfl_sync(kFull, base, 0);
+                if (base >= lvl_end) break;
+                const int nb = (int)(lvl_end - base < 32 ? lvl_end - base : 32);
+                int64_t eb = 0, ee = 0;
+                if (lane < nb) {
+                    const int32_t v = q[base + lane];
+                    eb = __ldg(in_off + v);
+                    ee = __ldg(in_off + v + 1);
+                    sexam += (unsigned long long)(ee - eb);
+                }
+                const int64_t g0 = eb >> 2;
+                const int64_t ng = ee > eb ? ((ee - 1) >> 2) - g0 + 1 : 0;
+                const int64_t incl = warp_incl_scan<int64_t>(ng, lane);
+                const int64_t total = __shfl_sync(kFull, incl, 31);
+                for (int64_t gb = 0; gb < total; gb += 32) {
+                    const int64_t t = gb + lane;
+                    int owner = 0;   // first lane whose inclusive group count exceeds t
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
+                        if (c <= t) owner += step;
+                    }
+                    const int64_t o_incl = __shfl_sync(kFull, incl, owner);
+                    const int64_t o_ng = __shfl_sync(kFull, ng, owner);
+                    const int64_t o_g0 = __shfl_sync(kFull, g0, owner);
+                    const int64_t o_eb = __shfl_sync(kFull, eb, owner);
+                    const int64_t o_ee = __shfl_sync(kFull, ee, owner);
+                    unsigned fresh = 0;
+                    int32_t src[4] = {0, 0, 0, 0};
+                    if (t < total)
+                        fresh = ic_group(wgt, in_src, o_g0 + (t - (o_incl - o_ng)), o_eb, o_ee, s, k0,
+                                         k1, vis, src);
+                    ic_append(fresh, src, lane, &s_tail, q);
+                }
+            }
+            __syncthreads();
+            head = lvl_end;
+        }
+        // emit: reserve the stage range, copy the queue, record size and offset
+        const long long len = (long long)s_tail;
+        unsigned long long ex = warp_sum<unsigned long long>(sexam);
+        if (lane == 0) s_red[0][warp] = ex;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int w2 = 0; w2 < kICBigThreads / 32; ++w2) tot += s_red[0][w2];
+            s_pos = atomicAdd(a.stage_cursor, (unsigned long long)len);
+            if ((long long)s_pos + len > a.stage_cap) {
+                raise_status(a.status, kDevStageOverflow);
+                a.sizes[j] = 0;
+                a.stage_off[j] = 0;
+                s_pos = ~0ull;
+            } else {
+                a.stage_off[j] = (int64_t)s_pos;
+                a.sizes[j] = (int32_t)len;
+                atomicAdd(a.examined, tot);
+                // 16 B offsets + 4 B write per member, 8 B per examined edge, 8 B per set
+                atomicAdd(a.alg_bytes, 8ull * tot + 20ull * (unsigned long long)len + 8ull);
+            }
+        }
+        __syncthreads();
+        if (s_pos != ~0ull)
+            for (long long x = threadIdx.x; x < len; x += blockDim.x) a.stage[s_pos + x] = q[x];
+        // clear this sample's visited bits
+        if (len > a.vis_words) {
+            for (int64_t x = threadIdx.x; x < a.vis_words; x += blockDim.x) vis[x] = 0u;
+        } else {
+            for (long long x = threadIdx.x; x < len; x += blockDim.x) vis[q[x] >> 5] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // LT: backward walk of the LT live-edge world.  Vertex v picks the first
 // in-edge whose running weight sum exceeds Philox(s, v, 0, pick tag).x; the
@@ -1190,16 +1358,18 @@ im_status run_sampling(const SamplingJob &job, const std::function<im_status(siz
         // second pass for sets longer than the per-walk queue: a few warps
         // with queues of n entries re-run exactly those samples
         const int64_t novf = (int64_t)hc[3];
-        int nb2 = (int)std::max<int64_t>(1, std::min<int64_t>((novf + kWarps - 1) / kWarps,
-                                                              num_sms()));
-        const int64_t warps2 = (int64_t)nb2 * kWarps;
-        const size_t need2 = (size_t)warps2 * (size_t)n * 4 +
-                             (model == IM_IC && !smem_vis ? (size_t)warps2 * vis_words * 4 : 0);
+        const bool ic_big = model == IM_IC;
+        // IC: one block per sample; LT: one walk per warp
+        const int64_t per_unit = (int64_t)n * 4 + (ic_big ? vis_words * 4 : 0);
+        int64_t units = ic_big ? std::min<int64_t>(novf, (int64_t)num_sms())
+                               : std::min<int64_t>((novf + kWarps - 1) / kWarps, num_sms()) * kWarps;
+        if (ic_big) units = std::max<int64_t>(1, std::min<int64_t>(units, (2ll << 30) / per_unit));
+        const int nb2 = (int)(ic_big ? units : std::max<int64_t>(1, units / kWarps));
+        const size_t need2 = (size_t)units * (size_t)per_unit;
         int32_t *q2 = nullptr;
         IM_CUDA(cudaMallocAsync((void **)&q2, need2, st));
-        uint32_t *vis2 = (uint32_t *)((char *)q2 + (size_t)warps2 * (size_t)n * 4);
-        if (model == IM_IC && !smem_vis)
-            IM_CUDA(cudaMemsetAsync(vis2, 0, (size_t)warps2 * vis_words * 4, st));
+        uint32_t *vis2 = (uint32_t *)((char *)q2 + (size_t)units * (size_t)n * 4);
+        if (ic_big) IM_CUDA(cudaMemsetAsync(vis2, 0, (size_t)units * vis_words * 4, st));
         IM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st));
         SampleArgs a2 = a;
         a2.list = a.ovf_list;
@@ -1207,9 +1377,15 @@ im_status run_sampling(const SamplingJob &job, const std::function<im_status(siz
         a2.queues = q2;
         a2.qcap = n;
         a2.gvis = vis2;
+        a2.vis_words = vis_words;
         a2.ovf_list = a.ovf_list + cnt;   // never written: qcap = n cannot overflow
         a = a2;
-        launch(nb2, 32);   // one walk per warp: queues of n entries for the longest sets
+        if (ic_big) {
+            KernelTimer kt(st, "sample_ic_big");
+            k_sample_ic_big<<<nb2, kICBigThreads, 0, st>>>(a);
+        } else {
+            launch(nb2, 32);   // one walk per warp: queues of n entries for the longest walks
+        }
         IM_CUDA(cudaGetLastError());
         IM_CUDA(cudaFreeAsync(q2, st));
         IM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
