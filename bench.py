@@ -61,11 +61,11 @@ WORKLOAD = ("rmat20-lt: R-MAT scale 20 (1,048,576 vertices, 16,777,216 edges, a/
             "seed 42), LT 1/in-degree as uint32, theta=4,194,304 RRR sets, k=100; plain greedy "
             "+ RandGreedi (148 partitions, streamed top ceil(k/4), delta=0.077)")
 # DRAM bytes per launch from an ncu capture, valid while the kernel source is
-# unchanged (sha256 of the file that holds it).  k_sample_lt1 was captured on
+# unchanged (sha256 of the kernel's source text, see kernel_sha).  k_sample_lt1 was captured on
 # the same graph at theta = 1,048,576 (42.82 M walk steps, 5.4886 GB read +
 # written, profiles/ncu_sample_lt1_rmat20_theta1M.txt); traffic grows with the
 # walk steps, so a full launch (171.49 M steps) moves 5.4886 * 171.49 / 42.82 GB.
-TRAFFIC: dict = {"sample_lt": {"src_sha": "5c730bde5ef0991b",
+TRAFFIC: dict = {"sample_lt": {"src_sha": "01f4f2f4afb7c106",
                                "bytes_per_launch": int(5.4886e9 * 171.49 / 42.82)}}
 
 
@@ -170,10 +170,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def src_sha(name: str) -> str:
+def kernel_sha(file: str, kernel: str) -> str:
+    """sha256 of one kernel's source text (from its __global__ line to the
+    brace that closes its body), so an ncu capture stays tied to that kernel
+    and not to unrelated edits of the same file."""
     import hashlib
-    path = os.path.join(ROOT, "paper_2408_10982_gb300", "csrc", name)
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    text = open(os.path.join(ROOT, "paper_2408_10982_gb300", "csrc", file)).read()
+    start = text.index(kernel + "(")
+    start = text.rindex("__global__", 0, start)
+    depth, i = 0, text.index("{", start)
+    while True:
+        if text[i] == "{":
+            depth += 1
+        elif text[i] == "}":
+            depth -= 1
+            if depth == 0:
+                break
+        i += 1
+    return hashlib.sha256(text[start:i + 1].encode()).hexdigest()[:16]
 
 
 # ---------------------------------------------------------------------------
@@ -300,7 +314,7 @@ def run_ours(args):
     dominant = max(per.items(), key=lambda kv: kv[1][1])[0]
     traffic = None
     tr = TRAFFIC.get(samp_name)
-    if tr and tr["src_sha"] == src_sha("sample.cu"):
+    if tr and tr["src_sha"] == kernel_sha("sample.cu", "k_sample_lt1"):
         traffic = tr["bytes_per_launch"]
     roofline = {"kernel": samp_name, "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
