@@ -384,7 +384,7 @@ def e2e(args, g, im, torch, dev, stream, first, dist):
     res = {k: torch.zeros(sz, dtype=dt).pin_memory() for k, sz, dt in
            (("seeds", K, torch.int32), ("gains", K, torch.int64), ("ns", 1, torch.int32),
             ("cov", 1, torch.int64))}
-    opts_rg = im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED, fused=True)
+    opts_rg = im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED, fused=bool(args.rg_fused))
     steps = max(1, min(args.steps, 3))
     examined = 0
 
