@@ -212,6 +212,31 @@ typedef enum {
 im_status im_tune_set(int32_t knob, int64_t value);
 im_status im_tune_get(int32_t knob, int64_t *value);
 
+/* Autotuner (not in the paper): times every allowed value of the knobs above
+ * on a probe of the caller's workload -- theta sets of graph g under model
+ * and seed -- and leaves the fastest values set (process-wide).  Tried: lanes
+ * per LT walk (LT only), counter replicas of the covering-subset build, and,
+ * when rg_opts asks for RandGreedi, its evaluation width and (two-launch mode)
+ * its bucket-stage layout, with rg_opts' partition count, alpha and delta.
+ * Results never depend on these knobs, so tuning changes only speed; the
+ * partition count itself is a parameter of the method and is not tuned.
+ *   out->lt_group, index_replicas, rg_evals, rg_cluster: the chosen values
+ *       (-1 where not tuned);
+ *   out->ms[row][i]: the best-of-two time of the i-th value tried (rows: LT
+ *       group {1, 8, 16, 32}, replicas {1, 2, 4, 8}, evaluation width
+ *       {1, 2, 4, 8}, bucket stage {0, 1, 2, 4, 8, -1}); -1 where not run.
+ * Allocates a probe pool (and a small result buffer) and frees them before it
+ * returns.  Synchronises the stream. */
+typedef struct {
+    int32_t lt_group;
+    int32_t index_replicas;
+    int32_t rg_evals;
+    int32_t rg_cluster;
+    double ms[4][8];
+} im_tune_result;
+im_status im_autotune(const im_graph *g, im_model model, uint64_t seed, int64_t theta, int32_t k,
+                      const im_cover_opts *rg_opts, im_tune_result *out, void *stream);
+
 /* ---- per-kernel device timing (tracing) -------------------------------------
  * While enabled, every kernel the library launches is bracketed by a pair of
  * CUDA events on its stream.  im_profile_read waits for the recorded events

@@ -95,6 +95,7 @@ def lib():
             "im_server_stats": ([vp, vp, vp, vp], ctypes.c_int),
             "im_batch_destroy": ([vp], ctypes.c_int),
             "im_spread": ([vp, ctypes.c_int, vp, i32, u64, u64, u64, vp, vp, vp, vp], ctypes.c_int),
+            "im_autotune": ([vp, ctypes.c_int, u64, i64, i32, vp, vp, vp], ctypes.c_int),
             "im_solve_batch": ([vp, vp, i32, i32, vp, vp, vp, vp], ctypes.c_int),
             "im_solve": ([vp, ctypes.c_int, i32, ctypes.c_double, ctypes.c_double, u64, vp, vp,
                           vp, vp, vp, vp, vp], ctypes.c_int),
@@ -314,6 +315,25 @@ def im_spread(g, model: int, seeds, seed: int, first_run: int, runs: int, activa
                            first_run, runs, _ptr(activated), _ptr(root_hit), ctypes.byref(total),
                            _stream(stream)), "im_spread")
     return total.value
+
+
+class TuneResult(ctypes.Structure):
+    """im_tune_result (see include/im.h)."""
+    _fields_ = [("lt_group", ctypes.c_int32), ("index_replicas", ctypes.c_int32),
+                ("rg_evals", ctypes.c_int32), ("rg_cluster", ctypes.c_int32),
+                ("ms", (ctypes.c_double * 8) * 4)]
+
+
+def im_autotune(g, model: int, seed: int, theta: int, k: int, rg_opts: CoverOpts | None = None,
+                stream=None) -> dict:
+    """Time the result-invariant knobs on a probe of the workload and keep the
+    fastest values; returns the chosen values and the measured times."""
+    r = TuneResult()
+    _check(lib().im_autotune(g.value if hasattr(g, "value") else g, model, seed, theta, k,
+                             None if rg_opts is None else ctypes.byref(rg_opts), ctypes.byref(r),
+                             _stream(stream)), "im_autotune")
+    return {"lt_group": r.lt_group, "index_replicas": r.index_replicas, "rg_evals": r.rg_evals,
+            "rg_cluster": r.rg_cluster, "ms": [[round(x, 3) for x in row] for row in r.ms]}
 
 
 class ServerOpts(ctypes.Structure):

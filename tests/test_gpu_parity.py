@@ -442,3 +442,29 @@ def test_spread_rejects_bad_seed(im):
         im.im_spread(G.handle, im.IM_IC, np.array([1, 30], np.int32), 1, 0, 10)
     assert e.value.status == im.IM_ERR_INVALID_ARG
     assert im.im_spread(G.handle, im.IM_IC, np.zeros(0, np.int32), 1, 0, 5) == 0
+
+
+def test_autotune_picks_allowed_values_and_keeps_results(im):
+    """im_autotune times the result-invariant knobs on a probe and leaves the
+    fastest values set; the pool and both covers still equal the oracle's."""
+    knobs = (im.IM_TUNE_LT_GROUP, im.IM_TUNE_RG_CLUSTER, im.IM_TUNE_INDEX_REPLICAS,
+             im.IM_TUNE_RG_EVALS)
+    saved = [im.im_tune_get(kn) for kn in knobs]
+    try:
+        g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+        G = im.Graph(g)
+        opts = im.cover_opts(im.IM_RANDGREEDI, 148, (1, 4), 0.077, 42, False)
+        r = im.im_autotune(G.handle, im.IM_LT, 42, 20000, 50, opts)
+        assert r["lt_group"] in (1, 8, 16, 32) and r["index_replicas"] in (1, 2, 4, 8)
+        assert r["rg_evals"] in (1, 2, 4, 8) and r["rg_cluster"] in (0, 1, 2, 4, 8, -1)
+        assert im.im_tune_get(im.IM_TUNE_LT_GROUP) == r["lt_group"]
+        assert im.im_tune_get(im.IM_TUNE_RG_CLUSTER) == r["rg_cluster"]
+        assert all(x >= 0 for x in r["ms"][0][:4]) and all(x >= 0 for x in r["ms"][3][:6])
+        _rg_compare(im, g, im.IM_LT, 30000, 50, 148, (1, 4), 0.077, False)
+        G2, P2 = gpu_pool(im, g, im.IM_LT, 7, [(0, 20000)])
+        assert_pool_equal(im, P2, O.sample(O.LT, g, 7, 0, 20000))
+        r_ic = im.im_autotune(G.handle, im.IM_IC, 3, 5000, 10)
+        assert r_ic["lt_group"] == -1 and r_ic["rg_evals"] == -1
+    finally:
+        for kn, v in zip(knobs, saved):
+            im.im_tune_set(kn, v)
