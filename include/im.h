@@ -48,7 +48,7 @@ typedef enum {
     IM_ERR_TIMEOUT = -4,       /* a bounded device wait expired (grid barrier, stream flag) */
     IM_ERR_CAPACITY = -5,      /* a pool or queue capacity was exceeded; state unchanged */
     IM_ERR_BUSY = -6,          /* the request is still running (serving poll) */
-    IM_ERR_UNSUPPORTED = -7    /* a valid request this build cannot run (e.g. no GPU) */
+    IM_ERR_UNSUPPORTED = -7    /* a valid request the library cannot run here (e.g. no GPU) */
 } im_status;
 
 typedef enum { IM_IC = 0, IM_LT = 1 } im_model;
