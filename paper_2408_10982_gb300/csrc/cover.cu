@@ -11,14 +11,17 @@
 //
 // RandGreedi: the paper's m sender machines are m "producer" blocks, each
 // running the lazy local greedy of one vertex part V_p (Alg. 2) with its
-// gains in shared memory and its own theta-bit covered bitmap; the receiver's
-// B bucketing
-// threads are B "consumer" blocks, one bucket each.  A producer publishes its
-// j-th seed (j < ceil(alpha k)) in slot (j, p) of a device array and raises a
-// release flag; consumers read the slots in (j, p) order with acquire loads,
-// so the buckets see the same stream order in every run.  In the fused mode
-// producers and consumers are one cooperative launch (co-resident), so the
-// aggregation overlaps the local greedy as in the paper's streaming design.
+// gains in shared memory and its own theta-bit covered bitmap.  A producer
+// publishes its j-th seed (j < ceil(alpha k)) in slot (j, p) of a device array
+// and raises a release flag; the buckets consume the slots in (j, p) order, so
+// they see the same stream order in every run.  The receiver's B bucketing
+// threads become, by default, k_rg_stream_masks after the producers finish:
+// one 64-bit mask per RRR set holds the buckets covering it, so one pass over
+// a streamed subset counts its gain for every bucket.  Alternatives (tuning
+// knob values): one "consumer" block or thread-block cluster per bucket, and
+// a fused mode where producers and consumers are one cooperative launch and
+// the consumers read the slots with acquire loads as they are published, the
+// paper's streaming overlap.
 #include <cooperative_groups.h>
 
 #include <algorithm>

@@ -1,16 +1,19 @@
 // sample.cu -- RRR sampling (IC reverse BFS, LT backward walk), compaction into
 // the pool's CSR, and the segmented sorts that put every set in ascending order.
 //
-// One warp owns one sample at a time and takes the next sample id from a
-// global counter (persistent kernel, dynamic balancing: set sizes are heavy
-// tailed on R-MAT graphs).  IC (Def. 3 under the IC live-edge world): the
-// warp expands up to 32 queued vertices at once; their in-edge ranges are
-// split into aligned groups of four edges, one group per lane, so each lane
-// makes one Philox call (four coins) and one 16-byte load of weights and one
-// of sources.  LT: the walk takes one step per iteration; the picked in-edge
-// (first edge whose running weight sum exceeds the draw) is found by a
-// 32-ary search over the per-vertex cumulative weights, the revisit test is a
-// warp compare against the path held in shared memory.
+// Every sampler is a persistent kernel that takes the next sample id from a
+// global counter (dynamic balancing: set sizes are heavy tailed on R-MAT).
+// IC (Def. 3 under the IC live-edge world): one warp per sample expands up to
+// 32 queued vertices at once; their in-edge ranges are split into aligned
+// groups of four edges, so each lane makes one Philox call (four coins) and
+// one 16-byte load of weights and one of sources per group.  Sets longer than
+// the warp's queue are re-run by k_sample_ic_big, one block per sample.  LT:
+// k_sample_lt1 (default) runs one walk per thread; the picked in-edge (first
+// edge whose running weight sum exceeds the draw) comes from a cut-point table
+// in O(1) expected loads, and revisits are tested through a per-walk Bloom
+// filter.  k_sample_lt<G> runs a walk per group of G lanes over a fanout-32
+// search tree (a tuning-knob alternative, and the second pass for walks longer
+// than the thread kernel's queue).
 #include <algorithm>
 #include <mutex>
 
