@@ -839,6 +839,26 @@ __global__ void k_lt_tree_sizes(const int64_t *in_off, int64_t n, int32_t *sizes
         sizes[v] = (int32_t)lt_tree_size(in_off[v + 1] - in_off[v]);
 }
 
+// Vertices with at most 32 in-edges (no upper tree levels): one thread each.
+__global__ void k_lt_index_small(const int64_t *in_off, const int32_t *in_src, const uint32_t *w,
+                                 const int64_t *tree_off, unsigned long long *leaf, uint4 *vrec,
+                                 int64_t n, int *invalid) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = in_off[v], e = in_off[v + 1], d = e - b;
+        if (d > 32) continue;   // k_lt_index
+        unsigned long long c = 0;
+        for (int64_t i = b; i < e; ++i) {
+            c += (unsigned long long)w[i];
+            leaf[i] = (c << 31) | (unsigned long long)(uint32_t)in_src[i];
+        }
+        if (c > (1ull << 32)) atomicExch(invalid, 1);
+        vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], 0u);
+    }
+}
+
+// Vertices with more than 32 in-edges: one warp each, running sums by warp
+// scans, then the upper levels of the fanout-32 tree.
 __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const uint32_t *w,
                            const int64_t *tree_off, unsigned long long *leaf,
                            unsigned long long *tree, uint4 *vrec, int64_t n, int *invalid) {
@@ -847,6 +867,7 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
     for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
          v += nw) {
         const int64_t b = in_off[v], e = in_off[v + 1], d = e - b;
+        if (d <= 32) continue;   // k_lt_index_small
         unsigned long long carry = 0;
         for (int64_t base = b; base < e; base += 32) {
             const int64_t i = base + lane;
@@ -1205,6 +1226,8 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
     IM_CUDA(cudaMalloc(&g->lt_vrec, (size_t)n * sizeof(uint4)));
     {
         KernelTimer kt(st, "lt_index");
+        k_lt_index_small<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, toff,
+                                                        g->lt_leaf, g->lt_vrec, n, d_invalid);
         k_lt_index<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, toff, g->lt_leaf,
                                                   g->lt_tree, g->lt_vrec, n, d_invalid);
     }
