@@ -93,6 +93,14 @@ const char *im_last_error(void);
 /* Library and device facts: number of SMs, device ordinal in use. */
 im_status im_device_info(int32_t *num_sms, int32_t *device);
 
+/* Device memory of graphs and pools comes from one stream-ordered memory pool
+ * per device.  Destroying a graph or pool returns its buffers to that pool,
+ * which keeps up to one eighth of the device's memory cached for the next
+ * graph or pool instead of unmapping it (the cache never holds a live
+ * buffer).  im_trim_memory waits for the current device to go idle and hands
+ * every cached byte back to the driver; IM_OK also when nothing is cached. */
+im_status im_trim_memory(void);
+
 /* ---- graph (Sec. 3.4 S1: the whole graph is replicated on every machine) --
  * in_off  int64[n+1]  in-CSR offsets (non-decreasing, in_off[0] = 0, in_off[n] = m)
  * in_src  int32[m]    source vertex of each in-edge; edges of a vertex in any

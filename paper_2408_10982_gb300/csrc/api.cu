@@ -119,16 +119,91 @@ int num_sms() {
     return cached[dev];
 }
 
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct DevHeap {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t st = nullptr;   // allocations and frees are ordered on this stream
+};
+
+std::mutex g_heap_mu;
+DevHeap g_heap[kMaxDevices];
+
+// The heap of the current device, created on first use.
+cudaError_t dev_heap(DevHeap **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_heap_mu);
+    DevHeap &h = g_heap[dev];
+    if (!h.pool) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        uint64_t keep = (uint64_t)total_b / 8;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaStream_t st = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        h.pool = pool;
+        h.st = st;
+    }
+    *out = &h;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+im_status dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    DevHeap *h = nullptr;
+    IM_CUDA(dev_heap(&h));
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, h->pool, h->st);
+    if (e == cudaErrorMemoryAllocation) {
+        // pages cached for sizes that do not fit: hand them back and retry once
+        cudaGetLastError();
+        IM_CUDA(cudaDeviceSynchronize());
+        cudaMemPoolTrimTo(h->pool, 0);
+        e = cudaMallocFromPoolAsync(p, bytes, h->pool, h->st);
+    }
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "device allocation");
+    }
+    // ordered before any later use on another stream
+    if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return cuda_fail(e, "device allocation");
+    return IM_OK;
+}
+
+void dev_free(void *p) {
+    if (!p) return;
+    DevHeap *h = nullptr;
+    if (dev_heap(&h) != cudaSuccess) return;
+    cudaDeviceSynchronize();   // no kernel on any stream may still use p
+    cudaFreeAsync(p, h->st);
+}
+
 im_status pool_scratch(im_pool *p, size_t bytes, void **out) {
     if (bytes > p->scratch_bytes) {
         if (p->scratch) {
-            IM_CUDA(cudaDeviceSynchronize());
-            cudaFree(p->scratch);
+            dev_free(p->scratch);
             p->scratch = nullptr;
             p->scratch_bytes = 0;
         }
         size_t want = bytes + bytes / 4 + 4096;
-        IM_CUDA(cudaMalloc(&p->scratch, want));
+        IM_TRY(dev_alloc(&p->scratch, want));
         p->scratch_bytes = want;
     }
     *out = p->scratch;
@@ -163,12 +238,11 @@ im_status copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st, bo
 im_status pool_results(im_pool *p, size_t bytes, void **out) {
     if (bytes > p->res_bytes) {
         if (p->res) {
-            IM_CUDA(cudaDeviceSynchronize());
-            cudaFree(p->res);
+            dev_free(p->res);
             p->res = nullptr;
             p->res_bytes = 0;
         }
-        IM_CUDA(cudaMalloc(&p->res, bytes));
+        IM_TRY(dev_alloc(&p->res, bytes));
         p->res_bytes = bytes;
     }
     *out = p->res;
@@ -213,6 +287,27 @@ im_status im_device_info(int32_t *sms, int32_t *device) {
     return IM_OK;
 }
 
+im_status im_trim_memory(void) {
+    int dev = 0, count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        set_error("no CUDA device");
+        return IM_ERR_UNSUPPORTED;
+    }
+    IM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return IM_OK;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_heap_mu);
+        pool = g_heap[dev].pool;
+    }
+    if (!pool) return IM_OK;
+    IM_CUDA(cudaDeviceSynchronize());
+    IM_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return IM_OK;
+}
+
 im_status im_graph_create(const int64_t *in_off, const int32_t *in_src, const uint32_t *w,
                           int64_t n, int64_t m, void *stream, im_graph **out) {
     if (!out || !in_off || n < 1 || n > INT32_MAX || m < 0 || m >= ((int64_t)1 << 31) ||
@@ -230,17 +325,18 @@ im_status im_graph_create(const int64_t *in_off, const int32_t *in_src, const ui
     g->m = m;
     const int64_t mpad = (m + 3) & ~(int64_t)3;   // 16-byte groups of four edges
     auto fail = [&](im_status s) {
-        cudaFree(g->in_off);
-        cudaFree(g->in_src);
-        cudaFree(g->w);
+        dev_free(g->in_off);
+        dev_free(g->in_src);
+        dev_free(g->w);
         delete g;
         return s;
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&g->in_off, (size_t)(n + 1) * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&g->in_src, (size_t)std::max<int64_t>(mpad, 4) * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&g->w, (size_t)std::max<int64_t>(mpad, 4) * 4)) != cudaSuccess)
-        return fail(cuda_fail(e, "im_graph_create: cudaMalloc"));
+    im_status as;
+    if ((as = dev_alloc(&g->in_off, (size_t)(n + 1) * 8)) != IM_OK ||
+        (as = dev_alloc(&g->in_src, (size_t)std::max<int64_t>(mpad, 4) * 4)) != IM_OK ||
+        (as = dev_alloc(&g->w, (size_t)std::max<int64_t>(mpad, 4) * 4)) != IM_OK)
+        return fail(as);
     if ((e = cudaMemcpyAsync(g->in_off, in_off, (size_t)(n + 1) * 8, cudaMemcpyDefault, st)) !=
             cudaSuccess ||
         (e = cudaMemsetAsync(g->in_src, 0, (size_t)std::max<int64_t>(mpad, 4) * 4, st)) !=
@@ -278,15 +374,10 @@ im_status im_graph_create(const int64_t *in_off, const int32_t *in_src, const ui
 im_status im_graph_destroy(im_graph *g) {
     if (!g) return IM_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
-    cudaFree(g->in_off);
-    cudaFree(g->in_src);
-    cudaFree(g->w);
-    cudaFree(g->lt_vrec);
-    cudaFree(g->lt_leaf);
-    cudaFree(g->lt_tree);
-    cudaFree(g->lt_guide);
-    cudaFree(g->out_off);
-    cudaFree(g->out_rec);
+    for (void *b : {(void *)g->in_off, (void *)g->in_src, (void *)g->w, (void *)g->lt_vrec,
+                    (void *)g->lt_leaf, (void *)g->lt_tree, (void *)g->lt_guide,
+                    (void *)g->out_off, (void *)g->out_rec})
+        dev_free(b);
     delete g;
     return IM_OK;
 }
@@ -320,16 +411,14 @@ im_status im_pool_create(const im_graph *g, int64_t max_sets, int64_t max_entrie
     p->max_entries = max_entries;
     const int64_t n = g->n;
     cudaError_t e;
-    if ((e = cudaMalloc(&p->set_off, (size_t)(max_sets + 1) * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&p->members, (size_t)std::max<int64_t>(max_entries, 1) * 4)) !=
-            cudaSuccess ||
-        (e = cudaMalloc(&p->vtx_off, (size_t)(n + 1) * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&p->set_ids, (size_t)std::max<int64_t>(max_entries, 1) * 4)) !=
-            cudaSuccess ||
-        (e = cudaMalloc(&p->vtx_cursor, (size_t)(kMaxIndexReplicas + 1) * n * 4)) != cudaSuccess) {
-        im_status s = cuda_fail(e, "im_pool_create: cudaMalloc");
+    im_status as;
+    if ((as = dev_alloc(&p->set_off, (size_t)(max_sets + 1) * 8)) != IM_OK ||
+        (as = dev_alloc(&p->members, (size_t)std::max<int64_t>(max_entries, 1) * 4)) != IM_OK ||
+        (as = dev_alloc(&p->vtx_off, (size_t)(n + 1) * 8)) != IM_OK ||
+        (as = dev_alloc(&p->set_ids, (size_t)std::max<int64_t>(max_entries, 1) * 4)) != IM_OK ||
+        (as = dev_alloc(&p->vtx_cursor, (size_t)(kMaxIndexReplicas + 1) * n * 4)) != IM_OK) {
         im_pool_destroy(p);
-        return s;
+        return as;
     }
     cudaMemset(p->set_off, 0, 8);
     cudaMemset(p->vtx_off, 0, (size_t)(n + 1) * 8);
@@ -345,18 +434,11 @@ im_status im_pool_create(const im_graph *g, int64_t max_sets, int64_t max_entrie
 im_status im_pool_destroy(im_pool *p) {
     if (!p) return IM_ERR_INVALID_ARG;
     DeviceGuard dg(p->device);
-    cudaFree(p->set_off);
-    cudaFree(p->members);
-    cudaFree(p->vtx_off);
-    cudaFree(p->set_ids);
-    cudaFree(p->vtx_cursor);
-    cudaFree(p->part);
-    cudaFree(p->part_off);
-    cudaFree(p->part_vtx);
-    cudaFree(p->part_loc);
-    cudaFree(p->rg_block);
-    cudaFree(p->scratch);
-    cudaFree(p->res);
+    for (void *b : {(void *)p->set_off, (void *)p->members, (void *)p->vtx_off,
+                    (void *)p->set_ids, (void *)p->vtx_cursor, (void *)p->part,
+                    (void *)p->part_off, (void *)p->part_vtx, (void *)p->part_loc,
+                    (void *)p->rg_block, p->scratch, p->res})
+        dev_free(b);
     delete p;
     return IM_OK;
 }

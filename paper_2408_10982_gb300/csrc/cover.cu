@@ -1179,10 +1179,10 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
                         align256((size_t)B * k * 4) + align256((size_t)B * k * 8) +
                         align256((size_t)(P + B) * 6 * 8);
     if (p->rg_cap_bytes < need) {
-        if (p->rg_block) cudaFree(p->rg_block);
+        dev_free(p->rg_block);
         p->rg_block = nullptr;
         p->rg_cap_bytes = 0;
-        IM_CUDA(cudaMalloc(&p->rg_block, need));
+        IM_TRY(dev_alloc(&p->rg_block, need));
         p->rg_cap_bytes = need;
     }
     {

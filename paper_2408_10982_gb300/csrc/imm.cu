@@ -28,13 +28,12 @@ im_status pool_grow(im_pool *p, int64_t max_sets, int64_t max_entries, cudaStrea
     if (max_sets == p->max_sets && max_entries == p->max_entries) return IM_OK;
     int64_t *so = nullptr;
     int32_t *mem = nullptr, *sid = nullptr;
-    if (cudaMalloc(&so, (size_t)(max_sets + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&mem, (size_t)std::max<int64_t>(max_entries, 1) * 4) != cudaSuccess ||
-        cudaMalloc(&sid, (size_t)std::max<int64_t>(max_entries, 1) * 4) != cudaSuccess) {
-        cudaFree(so);
-        cudaFree(mem);
-        cudaFree(sid);
-        cudaGetLastError();
+    if (dev_alloc(&so, (size_t)(max_sets + 1) * 8) != IM_OK ||
+        dev_alloc(&mem, (size_t)std::max<int64_t>(max_entries, 1) * 4) != IM_OK ||
+        dev_alloc(&sid, (size_t)std::max<int64_t>(max_entries, 1) * 4) != IM_OK) {
+        dev_free(so);
+        dev_free(mem);
+        dev_free(sid);
         set_error("pool growth: device memory exhausted");
         return IM_ERR_OOM;
     }
@@ -42,9 +41,9 @@ im_status pool_grow(im_pool *p, int64_t max_sets, int64_t max_entries, cudaStrea
     if (p->total > 0)
         IM_CUDA(cudaMemcpyAsync(mem, p->members, (size_t)p->total * 4, cudaMemcpyDeviceToDevice, st));
     IM_CUDA(cudaStreamSynchronize(st));
-    cudaFree(p->set_off);
-    cudaFree(p->members);
-    cudaFree(p->set_ids);
+    dev_free(p->set_off);
+    dev_free(p->members);
+    dev_free(p->set_ids);
     p->set_off = so;
     p->members = mem;
     p->set_ids = sid;

@@ -248,13 +248,15 @@ im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st
     if (p->part_valid && p->part_P == P && p->part_seed == pseed) return IM_OK;
     const int64_t n = p->g->n;
     if (!p->part) {
-        IM_CUDA(cudaMalloc(&p->part, (size_t)n * 4));
-        IM_CUDA(cudaMalloc(&p->part_vtx, (size_t)n * 4));
-        IM_CUDA(cudaMalloc(&p->part_loc, (size_t)n * 4));
+        IM_TRY(dev_alloc(&p->part, (size_t)n * 4));
+        IM_TRY(dev_alloc(&p->part_vtx, (size_t)n * 4));
+        IM_TRY(dev_alloc(&p->part_loc, (size_t)n * 4));
     }
     if (p->part_cap < P) {
-        if (p->part_off) cudaFree(p->part_off);
-        IM_CUDA(cudaMalloc(&p->part_off, (size_t)(P + 1) * 4));
+        dev_free(p->part_off);
+        p->part_off = nullptr;
+        p->part_cap = 0;
+        IM_TRY(dev_alloc(&p->part_off, (size_t)(P + 1) * 4));
         p->part_cap = P;
     }
     im_status s = launch_partition_labels(n, P, pseed, p->part, st);

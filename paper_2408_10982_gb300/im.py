@@ -67,6 +67,7 @@ def lib():
             "im_status_str": ([ctypes.c_int], ctypes.c_char_p),
             "im_last_error": ([], ctypes.c_char_p),
             "im_device_info": ([vp, vp], ctypes.c_int),
+            "im_trim_memory": ([], ctypes.c_int),
             "im_graph_create": ([vp, vp, vp, i64, i64, vp, pp], ctypes.c_int),
             "im_graph_destroy": ([vp], ctypes.c_int),
             "im_graph_info": ([vp, vp, vp, vp], ctypes.c_int),
@@ -162,6 +163,10 @@ def im_device_info():
     sms, dev = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().im_device_info(ctypes.byref(sms), ctypes.byref(dev)), "im_device_info")
     return sms.value, dev.value
+
+
+def im_trim_memory():
+    _check(lib().im_trim_memory(), "im_trim_memory")
 
 
 def im_graph_create(in_off, in_src, w, n: int, m: int, stream=None):

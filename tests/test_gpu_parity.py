@@ -468,3 +468,28 @@ def test_autotune_picks_allowed_values_and_keeps_results(im):
     finally:
         for kn, v in zip(knobs, saved):
             im.im_tune_set(kn, v)
+
+
+def test_device_heap_reuse_then_trim(im):
+    """Graphs and pools created after others were destroyed reuse their cached
+    device pages and still give the oracle's sets and the same cover;
+    im_trim_memory then hands the cache back to the driver."""
+    torch = pytest.importorskip("torch")
+    g = inputs.rmat_graph(1 << 12, 1 << 16, 5, "lt")
+    ref = oracle_pool(g, 1, 9, [(0, 3000)])
+    first = None
+    for cap in (1 << 22, 1 << 20, 1 << 23):
+        G, P = gpu_pool(im, g, 1, 9, [(0, 3000)], cap_entries=cap)
+        assert_pool_equal(im, P, ref)
+        c = P.cover(10)
+        got = (c.seeds.tolist(), c.gains.tolist(), c.coverage)
+        first = first or got
+        assert got == first
+        P.close()
+        G.close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    im.im_trim_memory()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 >= free0 + (16 << 20)      # the last pool alone cached 2 x 32 MB
+    im.im_trim_memory()                      # nothing left to hand back: still ok
