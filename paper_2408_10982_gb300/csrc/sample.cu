@@ -833,10 +833,21 @@ __device__ __forceinline__ int64_t lt_tree_size(int64_t d) {
     return total;
 }
 
-__global__ void k_lt_tree_sizes(const int64_t *in_off, int64_t n, int32_t *sizes) {
+// In-degree above which one block, not one warp, builds a vertex's running
+// sums (a warp on R-MAT's largest in-list, ~7 x 10^4 edges, is the whole build's
+// critical path).  At most m / (kLtBlockDeg + 1) vertices qualify.
+constexpr int64_t kLtBlockDeg = 1024;
+
+// Tree size of every vertex; lists the vertices of k_lt_index_block in big
+// (in no particular order; nbig counts them).
+__global__ void k_lt_tree_sizes(const int64_t *in_off, int64_t n, int32_t *sizes, int32_t *big,
+                                int *nbig) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        sizes[v] = (int32_t)lt_tree_size(in_off[v + 1] - in_off[v]);
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = in_off[v + 1] - in_off[v];
+        sizes[v] = (int32_t)lt_tree_size(d);
+        if (d > kLtBlockDeg) big[atomicAdd(nbig, 1)] = (int32_t)v;
+    }
 }
 
 // Vertices with at most 32 in-edges (no upper tree levels): one thread each.
@@ -867,7 +878,7 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
     for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
          v += nw) {
         const int64_t b = in_off[v], e = in_off[v + 1], d = e - b;
-        if (d <= 32) continue;   // k_lt_index_small
+        if (d <= 32 || d > kLtBlockDeg) continue;   // k_lt_index_small, k_lt_index_block
         unsigned long long carry = 0;
         for (int64_t base = b; base < e; base += 32) {
             const int64_t i = base + lane;
@@ -887,6 +898,63 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
         for (int l = L; l >= 1; --l) {
             const int64_t sz = (d + (1ll << (5 * l)) - 1) >> (5 * l);
             for (int64_t i = lane; i < sz; i += 32) {
+                const int64_t last = min((i + 1) << (5 * l), d) - 1;
+                lvl[i] = leaf[b + last] >> 31;
+            }
+            lvl += sz;
+        }
+    }
+}
+
+// Vertices with more than kLtBlockDeg in-edges: one block of 256 threads each,
+// 2048 edges per pass (8 consecutive ones per thread: sequential sums, then a
+// block scan of the thread totals), then the upper tree levels as above.
+__global__ void __launch_bounds__(256) k_lt_index_block(
+    const int64_t *in_off, const int32_t *in_src, const uint32_t *w, const int64_t *tree_off,
+    const int32_t *big, int nbig, unsigned long long *leaf, unsigned long long *tree, uint4 *vrec,
+    int *invalid) {
+    __shared__ unsigned long long wsum[8];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int j = blockIdx.x; j < nbig; j += gridDim.x) {
+        const int64_t v = big[j];
+        const int64_t b = in_off[v], e = in_off[v + 1], d = e - b;
+        unsigned long long carry = 0;
+        for (int64_t base = b; base < e; base += 2048) {
+            const int64_t i0 = base + (int64_t)tid * 8;
+            unsigned long long s[8], run = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                run += i0 + q < e ? (unsigned long long)w[i0 + q] : 0ull;
+                s[q] = run;
+            }
+            const unsigned long long incl = warp_incl_scan<unsigned long long>(run, lane);
+            if (lane == 31) wsum[wid] = incl;
+            __syncthreads();
+            unsigned long long before = 0, tot = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const unsigned long long x = wsum[q];
+                before += q < wid ? x : 0ull;
+                tot += x;
+            }
+            const unsigned long long off = carry + before + (incl - run);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (i0 + q < e)
+                    leaf[i0 + q] = ((off + s[q]) << 31) | (unsigned long long)(uint32_t)in_src[i0 + q];
+            carry += tot;
+            __syncthreads();   // wsum is rewritten by the next pass
+        }
+        if (tid == 0 && carry > (1ull << 32)) atomicExch(invalid, 1);
+        int L = 0;
+        for (int64_t t = d; t > 32; t = (t + 31) >> 5) ++L;
+        if (tid == 0)
+            vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], (uint32_t)L);
+        __syncthreads();   // every leaf of v written by the block is visible to it
+        unsigned long long *lvl = tree + tree_off[v];
+        for (int l = L; l >= 1; --l) {
+            const int64_t sz = (d + (1ll << (5 * l)) - 1) >> (5 * l);
+            for (int64_t i = tid; i < sz; i += blockDim.x) {
                 const int64_t last = min((i + 1) << (5 * l), d) - 1;
                 lvl[i] = leaf[b + last] >> 31;
             }
@@ -1203,33 +1271,51 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_lt_index_mu);
     if (g->lt_leaf) return IM_OK;
     const int64_t n = g->n, m = g->m;
-    int32_t *sizes = nullptr;
-    int64_t *toff = nullptr;
-    int *d_invalid = nullptr;
-    IM_CUDA(cudaMallocAsync((void **)&sizes, (size_t)n * 4, st));
-    IM_CUDA(cudaMallocAsync((void **)&toff, (size_t)(n + 1) * 8 + scan_tmp_bytes(n) + 256, st));
-    IM_CUDA(cudaMallocAsync((void **)&d_invalid, sizeof(int), st));
-    IM_CUDA(cudaMemsetAsync(d_invalid, 0, sizeof(int), st));
+    // stream-ordered temporaries, freed on every exit
+    struct Temps {
+        cudaStream_t st;
+        int32_t *sizes = nullptr, *big = nullptr;
+        int64_t *toff = nullptr;
+        int *flags = nullptr;   // [0] weights of some vertex sum above 2^32, [1] listed vertices
+        ~Temps() {
+            for (void *p : {(void *)sizes, (void *)big, (void *)toff, (void *)flags})
+                if (p) cudaFreeAsync(p, st);
+        }
+    } t{st};
+    const int64_t big_cap = m / (kLtBlockDeg + 1) + 1;
+    IM_CUDA(cudaMallocAsync((void **)&t.sizes, (size_t)n * 4, st));
+    IM_CUDA(cudaMallocAsync((void **)&t.big, (size_t)big_cap * 4, st));
+    IM_CUDA(cudaMallocAsync((void **)&t.toff, (size_t)(n + 1) * 8 + scan_tmp_bytes(n) + 256, st));
+    IM_CUDA(cudaMallocAsync((void **)&t.flags, 2 * sizeof(int), st));
+    IM_CUDA(cudaMemsetAsync(t.flags, 0, 2 * sizeof(int), st));
     {
         KernelTimer kt(st, "lt_index");
-        k_lt_tree_sizes<<<num_sms() * 4, 256, 0, st>>>(g->in_off, n, sizes);
+        k_lt_tree_sizes<<<num_sms() * 4, 256, 0, st>>>(g->in_off, n, t.sizes, t.big, t.flags + 1);
     }
-    void *scan_tmp = (char *)toff + (((size_t)(n + 1) * 8 + 255) & ~(size_t)255);
-    im_status rs = exclusive_scan_i32_to_i64(sizes, toff, n, nullptr, scan_tmp, scan_tmp_bytes(n),
-                                             st);
-    if (rs != IM_OK) return rs;
+    void *scan_tmp = (char *)t.toff + (((size_t)(n + 1) * 8 + 255) & ~(size_t)255);
+    IM_TRY(exclusive_scan_i32_to_i64(t.sizes, t.toff, n, nullptr, scan_tmp, scan_tmp_bytes(n), st));
     int64_t tree_total = 0;
-    IM_CUDA(cudaMemcpyAsync(&tree_total, toff + n, 8, cudaMemcpyDeviceToHost, st));
+    int nbig = 0;
+    IM_CUDA(cudaMemcpyAsync(&tree_total, t.toff + n, 8, cudaMemcpyDeviceToHost, st));
+    IM_CUDA(cudaMemcpyAsync(&nbig, t.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaStreamSynchronize(st));
+    if (nbig < 0 || nbig > big_cap) {
+        set_error("LT index: vertex list out of range");
+        return IM_ERR_CUDA;
+    }
     IM_TRY(dev_alloc(&g->lt_leaf, (size_t)std::max<int64_t>(m, 1) * 8));
     IM_TRY(dev_alloc(&g->lt_tree, (size_t)std::max<int64_t>(tree_total, 1) * 8));
     IM_TRY(dev_alloc(&g->lt_vrec, (size_t)n * sizeof(uint4)));
     {
         KernelTimer kt(st, "lt_index");
-        k_lt_index_small<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, toff,
-                                                        g->lt_leaf, g->lt_vrec, n, d_invalid);
-        k_lt_index<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, toff, g->lt_leaf,
-                                                  g->lt_tree, g->lt_vrec, n, d_invalid);
+        k_lt_index_small<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, t.toff,
+                                                        g->lt_leaf, g->lt_vrec, n, t.flags);
+        k_lt_index<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, t.toff, g->lt_leaf,
+                                                  g->lt_tree, g->lt_vrec, n, t.flags);
+        if (nbig > 0)
+            k_lt_index_block<<<std::min(nbig, num_sms() * 8), 256, 0, st>>>(
+                g->in_off, g->in_src, g->w, t.toff, t.big, nbig, g->lt_leaf, g->lt_tree,
+                g->lt_vrec, t.flags);
     }
     IM_CUDA(cudaGetLastError());
     IM_TRY(dev_alloc(&g->lt_guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
@@ -1239,10 +1325,7 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
     }
     IM_CUDA(cudaGetLastError());
     int invalid = 0;
-    IM_CUDA(cudaMemcpyAsync(&invalid, d_invalid, sizeof(int), cudaMemcpyDeviceToHost, st));
-    IM_CUDA(cudaFreeAsync(sizes, st));
-    IM_CUDA(cudaFreeAsync(toff, st));
-    IM_CUDA(cudaFreeAsync(d_invalid, st));
+    IM_CUDA(cudaMemcpyAsync(&invalid, t.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaStreamSynchronize(st));
     g->lt_valid = invalid ? 0 : 1;
     return IM_OK;

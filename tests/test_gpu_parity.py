@@ -493,3 +493,48 @@ def test_device_heap_reuse_then_trim(im):
     free1 = torch.cuda.mem_get_info()[0]
     assert free1 >= free0 + (16 << 20)      # the last pool alone cached 2 x 32 MB
     im.im_trim_memory()                      # nothing left to hand back: still ok
+
+
+def _hub_graph(seed):
+    """Hubs 0..7 with in-degrees on both sides of the index build's three
+    kernels (one thread up to 32 in-edges, one warp up to 1024, one block of
+    2048-edge passes beyond); every other vertex has in-edges from two hubs,
+    so LT walks keep passing through the hubs' search trees.  Random LT
+    weights with per-vertex sums below 2^32."""
+    rng = np.random.default_rng(seed)
+    n = 6000
+    hub_deg = [33, 1024, 1025, 2047, 2048, 2049, 4097, 5900]
+    src, dst = [], []
+    for h, d in enumerate(hub_deg):
+        s = rng.choice(np.arange(8, n), size=d, replace=False)
+        src += s.tolist()
+        dst += [h] * d
+    for v in range(8, n):
+        s = rng.choice(8, size=2, replace=False)
+        src += s.tolist()
+        dst += [v, v]
+    in_off, in_src = inputs.in_csr(n, np.array(src), np.array(dst))
+    w = np.zeros(in_src.size, np.uint32)
+    for v in range(n):
+        b, e = int(in_off[v]), int(in_off[v + 1])
+        parts = rng.dirichlet(np.ones(e - b + 1))[: e - b]
+        w[b:e] = np.floor(parts * inputs.U32_MAX).astype(np.uint32)
+    return inputs.Graph(n, in_off, in_src, w)
+
+
+def test_lt_index_hub_degrees_match_oracle(im):
+    g = _hub_graph(17)
+    ids = [(0, 12000), (12000, 8000)]
+    G, P = gpu_pool(im, g, im.IM_LT, 23, ids, cap_entries=1 << 24)
+    assert im.im_graph_info(G.handle)[2] == 1
+    assert_pool_equal(im, P, oracle_pool(g, 1, 23, ids))
+
+
+@pytest.mark.parametrize("hub", [1, 5])       # in-degree 1024 (warp), 2049 (block)
+def test_lt_index_flags_weights_above_one(im, hub):
+    g = _hub_graph(17)
+    w = g.w.copy()
+    b, e = int(g.in_off[hub]), int(g.in_off[hub + 1])
+    w[b:e] = np.uint32(1 << 23)               # sum (e - b) 2^23 > 2^32
+    G = im.Graph(inputs.Graph(g.n, g.in_off, g.in_src, w))
+    assert im.im_graph_info(G.handle)[2] == 0
