@@ -93,12 +93,13 @@ const char *im_last_error(void);
 /* Library and device facts: number of SMs, device ordinal in use. */
 im_status im_device_info(int32_t *num_sms, int32_t *device);
 
-/* Device memory of graphs and pools comes from one stream-ordered memory pool
- * per device.  Destroying a graph or pool returns its buffers to that pool,
- * which keeps up to one eighth of the device's memory cached for the next
- * graph or pool instead of unmapping it (the cache never holds a live
- * buffer).  im_trim_memory waits for the current device to go idle and hands
- * every cached byte back to the driver; IM_OK also when nothing is cached. */
+/* Device memory of RRR pools comes from one stream-ordered memory pool per
+ * device (graphs use plain cudaMalloc).  Destroying an RRR pool returns its
+ * buffers to that memory pool, which keeps up to one eighth of the device's
+ * memory cached for the next RRR pool instead of unmapping it (the cache
+ * never holds a live buffer).  im_trim_memory waits for the current device
+ * to go idle and hands every cached byte back to the driver; IM_OK also when
+ * nothing is cached. */
 im_status im_trim_memory(void);
 
 /* ---- graph (Sec. 3.4 S1: the whole graph is replicated on every machine) --

@@ -325,18 +325,17 @@ im_status im_graph_create(const int64_t *in_off, const int32_t *in_src, const ui
     g->m = m;
     const int64_t mpad = (m + 3) & ~(int64_t)3;   // 16-byte groups of four edges
     auto fail = [&](im_status s) {
-        dev_free(g->in_off);
-        dev_free(g->in_src);
-        dev_free(g->w);
+        cudaFree(g->in_off);
+        cudaFree(g->in_src);
+        cudaFree(g->w);
         delete g;
         return s;
     };
     cudaError_t e;
-    im_status as;
-    if ((as = dev_alloc(&g->in_off, (size_t)(n + 1) * 8)) != IM_OK ||
-        (as = dev_alloc(&g->in_src, (size_t)std::max<int64_t>(mpad, 4) * 4)) != IM_OK ||
-        (as = dev_alloc(&g->w, (size_t)std::max<int64_t>(mpad, 4) * 4)) != IM_OK)
-        return fail(as);
+    if ((e = cudaMalloc(&g->in_off, (size_t)(n + 1) * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&g->in_src, (size_t)std::max<int64_t>(mpad, 4) * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&g->w, (size_t)std::max<int64_t>(mpad, 4) * 4)) != cudaSuccess)
+        return fail(cuda_fail(e, "im_graph_create: cudaMalloc"));
     if ((e = cudaMemcpyAsync(g->in_off, in_off, (size_t)(n + 1) * 8, cudaMemcpyDefault, st)) !=
             cudaSuccess ||
         (e = cudaMemsetAsync(g->in_src, 0, (size_t)std::max<int64_t>(mpad, 4) * 4, st)) !=
@@ -377,7 +376,7 @@ im_status im_graph_destroy(im_graph *g) {
     for (void *b : {(void *)g->in_off, (void *)g->in_src, (void *)g->w, (void *)g->lt_vrec,
                     (void *)g->lt_leaf, (void *)g->lt_tree, (void *)g->lt_guide,
                     (void *)g->out_off, (void *)g->out_rec})
-        dev_free(b);
+        cudaFree(b);
     delete g;
     return IM_OK;
 }

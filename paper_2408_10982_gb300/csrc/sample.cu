@@ -1303,9 +1303,9 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
         set_error("LT index: vertex list out of range");
         return IM_ERR_CUDA;
     }
-    IM_TRY(dev_alloc(&g->lt_leaf, (size_t)std::max<int64_t>(m, 1) * 8));
-    IM_TRY(dev_alloc(&g->lt_tree, (size_t)std::max<int64_t>(tree_total, 1) * 8));
-    IM_TRY(dev_alloc(&g->lt_vrec, (size_t)n * sizeof(uint4)));
+    IM_CUDA(cudaMalloc(&g->lt_leaf, (size_t)std::max<int64_t>(m, 1) * 8));
+    IM_CUDA(cudaMalloc(&g->lt_tree, (size_t)std::max<int64_t>(tree_total, 1) * 8));
+    IM_CUDA(cudaMalloc(&g->lt_vrec, (size_t)n * sizeof(uint4)));
     {
         KernelTimer kt(st, "lt_index");
         k_lt_index_small<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, t.toff,
@@ -1318,7 +1318,7 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
                 g->lt_vrec, t.flags);
     }
     IM_CUDA(cudaGetLastError());
-    IM_TRY(dev_alloc(&g->lt_guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
+    IM_CUDA(cudaMalloc(&g->lt_guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
     if (m > 0) {
         KernelTimer kt(st, "lt_index");
         k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->lt_leaf, n, m, g->lt_guide);

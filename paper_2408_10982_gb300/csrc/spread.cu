@@ -223,8 +223,8 @@ im_status build_out_index(im_graph *g, cudaStream_t st) {
     void *scan_tmp = nullptr;
     IM_CUDA(cudaMallocAsync((void **)&cnt, (size_t)n * 4, st));
     IM_CUDA(cudaMallocAsync(&scan_tmp, scan_tmp_bytes(n), st));
-    IM_TRY(dev_alloc(&g->out_off, (size_t)(n + 1) * 8));
-    IM_TRY(dev_alloc(&g->out_rec, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
+    IM_CUDA(cudaMalloc(&g->out_off, (size_t)(n + 1) * 8));
+    IM_CUDA(cudaMalloc(&g->out_rec, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
     IM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * 4, st));
     {
         KernelTimer kt(st, "out_index");

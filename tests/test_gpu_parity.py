@@ -471,8 +471,8 @@ def test_autotune_picks_allowed_values_and_keeps_results(im):
 
 
 def test_device_heap_reuse_then_trim(im):
-    """Graphs and pools created after others were destroyed reuse their cached
-    device pages and still give the oracle's sets and the same cover;
+    """Pools created after others were destroyed reuse their cached device
+    pages and still give the oracle's sets and the same cover;
     im_trim_memory then hands the cache back to the driver."""
     torch = pytest.importorskip("torch")
     g = inputs.rmat_graph(1 << 12, 1 << 16, 5, "lt")
