@@ -7,8 +7,9 @@ fresh samples (ids after the rounds' ids) and a final SelectSeeds.  The
 formulas of Estimate / CheckGoodness / f are not in the paper (it defers to
 Tang et al. 2015 and Chen 2018); orc_imm_* in oracle.c writes them out.
 Parity unpinned: nothing in the paper fixes these numbers; the tests check
-the structure (doubling, stopping rule, final count) and the GPU's identity
-with this driver.
+the structure (doubling, stopping rule, final count), the guarantee the paper
+restates (seeds within 1 - 1/e - eps of the optimum, exact on tiny graphs) and
+the GPU's identity with this driver.
 """
 from __future__ import annotations
 
