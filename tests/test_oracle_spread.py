@@ -69,3 +69,20 @@ def test_special_cases(orc):
     adj = sp.csr_matrix((np.ones(g1.m), (g1.in_src, dst)), shape=(n, n))
     reach = breadth_first_order(adj, 4, directed=True, return_predecessors=False)
     assert np.all(act == len(reach))
+
+
+@pytest.mark.parametrize("model,wmode,gseed", [(0, "random", 31), (0, "0.3", 32),
+                                               (1, "lt_random", 33), (1, "lt", 34)])
+def test_ris_identity_exact_between_the_brute_forces(model, wmode, gseed):
+    """The identity RIS rests on (Def. 3, Sec. 2.1): sigma(S) = n P[S meets
+    RRR(r)] for a uniform root r; for one seed v, sigma({v}) = sum over roots
+    r of P[v in RRR(r)].  Forward reach over every live-edge world and reverse
+    reach (IC) / the backward pick chain (LT) from every root are independent
+    brute-force computations; they must agree exactly, as rationals."""
+    from oracle import brute
+    g = inputs.random_graph(5, 8, gseed, wmode)
+    incl = brute.ic_inclusion_exact if model == 0 else brute.lt_inclusion_exact
+    spread = brute.ic_spread_exact if model == 0 else brute.lt_spread_exact
+    per_root = [incl(g, r) for r in range(g.n)]
+    for v in range(g.n):
+        assert sum(pr[v] for pr in per_root) == spread(g, [v])
