@@ -2,7 +2,9 @@
 //
 // Each entry point validates its arguments, runs the kernels of sample.cu,
 // index.cu and cover.cu on the caller's stream, and maps device status words
-// and CUDA errors to im_status.  No C++ exception crosses the boundary.
+// and CUDA errors to im_status.  No C++ exception crosses the boundary.  The
+// device memory of RRR pools comes from dev_alloc / dev_free below (a cached
+// stream-ordered memory pool per device); graphs use plain cudaMalloc.
 #include <algorithm>
 #include <cstring>
 #include <map>

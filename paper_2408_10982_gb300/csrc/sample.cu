@@ -13,7 +13,10 @@
 // in O(1) expected loads, and revisits are tested through a per-walk Bloom
 // filter.  k_sample_lt<G> runs a walk per group of G lanes over a fanout-32
 // search tree (a tuning-knob alternative, and the second pass for walks longer
-// than the thread kernel's queue).
+// than the thread kernel's queue).  The LT index they read (running sums,
+// tree, cut points) is built once per graph by build_lt_index: in-lists of up
+// to 32 edges get their running sums from one thread each, up to 1024 from a
+// warp, longer ones from a block.
 #include <algorithm>
 #include <mutex>
 
