@@ -388,7 +388,7 @@ def e2e(args, g, im, torch, dev, stream, first, dist):
            (("seeds", K, torch.int32), ("gains", K, torch.int64), ("ns", 1, torch.int32),
             ("cov", 1, torch.int64))}
     opts_rg = im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED, fused=bool(args.rg_fused))
-    steps = max(1, min(args.steps, 3))
+    steps = max(1, min(args.steps, 10))
     examined = 0
 
     def one():
