@@ -389,7 +389,7 @@ im_status im_graph_info(const im_graph *g, int64_t *n, int64_t *m, int32_t *lt_v
     if (n) *n = g->n;
     if (m) *m = g->m;
     if (lt_valid) {
-        if (!g->lt_leaf) IM_TRY(build_lt_index(const_cast<im_graph *>(g), 0));
+        IM_TRY(build_lt_index(const_cast<im_graph *>(g), 0));   // returns at once when built
         *lt_valid = g->lt_valid;
     }
     return IM_OK;

@@ -1272,7 +1272,7 @@ static std::mutex g_lt_index_mu;   // graphs are shared by serving workers
 
 im_status build_lt_index(im_graph *g, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_lt_index_mu);
-    if (g->lt_leaf) return IM_OK;
+    if (g->lt_leaf) return IM_OK;   // set only once the whole index is built
     const int64_t n = g->n, m = g->m;
     // stream-ordered temporaries, freed on every exit
     struct Temps {
@@ -1285,6 +1285,18 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
                 if (p) cudaFreeAsync(p, st);
         }
     } t{st};
+    // the index itself: handed to g once complete, freed on any failure
+    struct Index {
+        unsigned long long *leaf = nullptr, *tree = nullptr;
+        uint4 *vrec = nullptr, *guide = nullptr;
+        ~Index() {
+            if (leaf || tree || vrec || guide) {
+                cudaDeviceSynchronize();
+                for (void *p : {(void *)leaf, (void *)tree, (void *)vrec, (void *)guide})
+                    cudaFree(p);
+            }
+        }
+    } x;
     const int64_t big_cap = m / (kLtBlockDeg + 1) + 1;
     IM_CUDA(cudaMallocAsync((void **)&t.sizes, (size_t)n * 4, st));
     IM_CUDA(cudaMallocAsync((void **)&t.big, (size_t)big_cap * 4, st));
@@ -1306,31 +1318,37 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
         set_error("LT index: vertex list out of range");
         return IM_ERR_CUDA;
     }
-    IM_CUDA(cudaMalloc(&g->lt_leaf, (size_t)std::max<int64_t>(m, 1) * 8));
-    IM_CUDA(cudaMalloc(&g->lt_tree, (size_t)std::max<int64_t>(tree_total, 1) * 8));
-    IM_CUDA(cudaMalloc(&g->lt_vrec, (size_t)n * sizeof(uint4)));
+    IM_CUDA(cudaMalloc(&x.leaf, (size_t)std::max<int64_t>(m, 1) * 8));
+    IM_CUDA(cudaMalloc(&x.tree, (size_t)std::max<int64_t>(tree_total, 1) * 8));
+    IM_CUDA(cudaMalloc(&x.vrec, (size_t)n * sizeof(uint4)));
     {
         KernelTimer kt(st, "lt_index");
         k_lt_index_small<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, t.toff,
-                                                        g->lt_leaf, g->lt_vrec, n, t.flags);
-        k_lt_index<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, t.toff, g->lt_leaf,
-                                                  g->lt_tree, g->lt_vrec, n, t.flags);
+                                                        x.leaf, x.vrec, n, t.flags);
+        k_lt_index<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, t.toff, x.leaf,
+                                                  x.tree, x.vrec, n, t.flags);
         if (nbig > 0)
             k_lt_index_block<<<std::min(nbig, num_sms() * 8), 256, 0, st>>>(
-                g->in_off, g->in_src, g->w, t.toff, t.big, nbig, g->lt_leaf, g->lt_tree,
-                g->lt_vrec, t.flags);
+                g->in_off, g->in_src, g->w, t.toff, t.big, nbig, x.leaf, x.tree, x.vrec,
+                t.flags);
     }
     IM_CUDA(cudaGetLastError());
-    IM_CUDA(cudaMalloc(&g->lt_guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
+    IM_CUDA(cudaMalloc(&x.guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
     if (m > 0) {
         KernelTimer kt(st, "lt_index");
-        k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->lt_leaf, n, m, g->lt_guide);
+        k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, x.leaf, n, m, x.guide);
     }
     IM_CUDA(cudaGetLastError());
     int invalid = 0;
     IM_CUDA(cudaMemcpyAsync(&invalid, t.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaStreamSynchronize(st));
     g->lt_valid = invalid ? 0 : 1;
+    g->lt_tree = x.tree;
+    g->lt_vrec = x.vrec;
+    g->lt_guide = x.guide;
+    g->lt_leaf = x.leaf;
+    x.leaf = x.tree = nullptr;
+    x.vrec = x.guide = nullptr;
     return IM_OK;
 }
 

@@ -24,7 +24,6 @@ namespace im {
 namespace {
 
 constexpr int kSpreadThreads = 512;
-constexpr int kSpreadWarps = kSpreadThreads / 32;
 
 // Out-edge index: for every source u, one 16-byte record per out-edge
 // {head v, in-CSR id e, w[e], lo(e)} where lo(e) is v's running in-weight sum
@@ -217,34 +216,50 @@ std::mutex g_out_index_mu;   // graphs are shared between threads
 
 im_status build_out_index(im_graph *g, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_out_index_mu);
-    if (g->out_off) return IM_OK;
+    if (g->out_off) return IM_OK;   // set only once the whole index is built
     const int64_t n = g->n, m = g->m;
-    int32_t *cnt = nullptr;
-    void *scan_tmp = nullptr;
-    IM_CUDA(cudaMallocAsync((void **)&cnt, (size_t)n * 4, st));
-    IM_CUDA(cudaMallocAsync(&scan_tmp, scan_tmp_bytes(n), st));
-    IM_CUDA(cudaMalloc(&g->out_off, (size_t)(n + 1) * 8));
-    IM_CUDA(cudaMalloc(&g->out_rec, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
-    IM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * 4, st));
+    // stream-ordered temporaries, freed on every exit; the index itself is
+    // handed to g once complete and freed on any failure
+    struct Parts {
+        cudaStream_t st;
+        int32_t *cnt = nullptr;
+        void *scan_tmp = nullptr;
+        int64_t *off = nullptr;
+        uint4 *rec = nullptr;
+        ~Parts() {
+            if (off || rec) {
+                cudaDeviceSynchronize();
+                cudaFree(off);
+                cudaFree(rec);
+            }
+            if (cnt) cudaFreeAsync(cnt, st);
+            if (scan_tmp) cudaFreeAsync(scan_tmp, st);
+        }
+    } t{st};
+    IM_CUDA(cudaMallocAsync((void **)&t.cnt, (size_t)n * 4, st));
+    IM_CUDA(cudaMallocAsync(&t.scan_tmp, scan_tmp_bytes(n), st));
+    IM_CUDA(cudaMalloc(&t.off, (size_t)(n + 1) * 8));
+    IM_CUDA(cudaMalloc(&t.rec, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
+    IM_CUDA(cudaMemsetAsync(t.cnt, 0, (size_t)n * 4, st));
     {
         KernelTimer kt(st, "out_index");
-        if (m > 0) k_out_hist<<<num_sms() * 4, 256, 0, st>>>(g->in_src, m, cnt);
+        if (m > 0) k_out_hist<<<num_sms() * 4, 256, 0, st>>>(g->in_src, m, t.cnt);
     }
     IM_CUDA(cudaGetLastError());
-    im_status s = exclusive_scan_i32_to_i64(cnt, g->out_off, n, nullptr, scan_tmp,
-                                            scan_tmp_bytes(n), st);
-    if (s != IM_OK) return s;
-    IM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * 4, st));
+    IM_TRY(exclusive_scan_i32_to_i64(t.cnt, t.off, n, nullptr, t.scan_tmp, scan_tmp_bytes(n), st));
+    IM_CUDA(cudaMemsetAsync(t.cnt, 0, (size_t)n * 4, st));
     {
         KernelTimer kt(st, "out_index");
         if (m > 0)
-            k_out_fill<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, n, g->out_off,
-                                                      cnt, g->out_rec);
+            k_out_fill<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, n, t.off,
+                                                      t.cnt, t.rec);
     }
     IM_CUDA(cudaGetLastError());
-    IM_CUDA(cudaFreeAsync(cnt, st));
-    IM_CUDA(cudaFreeAsync(scan_tmp, st));
     IM_CUDA(cudaStreamSynchronize(st));
+    g->out_rec = t.rec;
+    g->out_off = t.off;
+    t.off = nullptr;
+    t.rec = nullptr;
     return IM_OK;
 }
 
