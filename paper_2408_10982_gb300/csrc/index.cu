@@ -247,11 +247,10 @@ im_status build_index(im_pool *p, cudaStream_t st) {
 im_status build_partition(im_pool *p, int32_t P, uint64_t pseed, cudaStream_t st) {
     if (p->part_valid && p->part_P == P && p->part_seed == pseed) return IM_OK;
     const int64_t n = p->g->n;
-    if (!p->part) {
-        IM_TRY(dev_alloc(&p->part, (size_t)n * 4));
-        IM_TRY(dev_alloc(&p->part_vtx, (size_t)n * 4));
-        IM_TRY(dev_alloc(&p->part_loc, (size_t)n * 4));
-    }
+    p->part_valid = false;   // until this build completes
+    if (!p->part) IM_TRY(dev_alloc(&p->part, (size_t)n * 4));
+    if (!p->part_vtx) IM_TRY(dev_alloc(&p->part_vtx, (size_t)n * 4));
+    if (!p->part_loc) IM_TRY(dev_alloc(&p->part_loc, (size_t)n * 4));
     if (p->part_cap < P) {
         dev_free(p->part_off);
         p->part_off = nullptr;
