@@ -220,6 +220,7 @@ im_status grow(void **p, size_t *have, size_t need) {
     const size_t want = need + need / 4 + 4096;
     if (cudaMalloc(p, want) != cudaSuccess) {
         cudaGetLastError();
+        *p = nullptr;
         set_error("im_solve_batch: device memory exhausted");
         return IM_ERR_OOM;
     }
