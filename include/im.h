@@ -129,8 +129,13 @@ im_status im_pool_destroy(im_pool *p);
 /* Drop every set (theta = 0) without freeing memory. */
 im_status im_pool_reset(im_pool *p);
 /* theta, total entries T, and the edges examined by all sampling so far
- * (IC: every in-edge of every member; LT: in-edges up to and including the
- * picked one, or all in-edges when none is picked). */
+ * (IC: every in-edge of every member, each read and given a coin; LT: the
+ * in-edges a cumulative-weight scan would decide over -- up to and including
+ * the picked one, or all in-edges when none is picked.  The LT sampler does
+ * not read these edges: a cut-point table decides the pick with one load, so
+ * for LT this count is a measure of the work a scan-based sampler does, not of
+ * this one's memory traffic.  A walk of L members makes L draws, so LT walk
+ * steps = T). */
 im_status im_pool_info(const im_pool *p, int64_t *theta, int64_t *total, int64_t *examined);
 
 /* ---- Sample (Alg. 1 "Sample"; Def. 3; Sec. 2.1) ------------------------------
@@ -182,10 +187,18 @@ im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out
  * on-chip and not counted):
  *   IC: per member 16 (its in-CSR offset pair) + 4 (member write),
  *       per examined edge 8 (source id + weight), per set 8 (offset);
- *   LT: per walk step at a vertex of in-degree d: 16 (offset pair)
- *       + 8 (floor(log2 d) + 1) when d > 0 (binary search of the cumulative
- *       weights) + 4 when an edge is picked (its source) + 4 (member write),
- *       per set 8 (offset). */
+ *   LT, one walk per thread (the default): per set 8 (offset) + 16 (the
+ *       root's vertex record) + 4 (root write); per step at a vertex with
+ *       in-degree d > 0: 32 (one cut point); when the draw lies past the cut
+ *       point's edge, 8 per binary-search probe actually made, plus 8 + 16
+ *       (the picked leaf and its source's vertex record); 4 per member added.
+ *   LT, G lanes per walk: per walk step at a vertex of in-degree d: 16
+ *       (offset pair) + 8 (floor(log2 d) + 1) when d > 0 (search of the
+ *       cumulative weights) + 4 when an edge is picked (its source) + 4
+ *       (member write), per set 8 (offset).
+ * These are the bytes the kernels' own loads need, not a linear scan of the
+ * in-edges the examined-edge count covers (the LT pick reads one cut point,
+ * not the e + 1 edges it decides over). */
 im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
 
 /* ---- tuning knobs (process-wide; results never depend on them) ---------------
@@ -276,12 +289,19 @@ im_status im_randgreedi_stats(const im_pool *p, int64_t *stats, void *stream);
  * and the covering subsets (vtx_off int64[n+1], set_ids int32[T]) -- e.g. as
  * exported by im_pool_export / im_index_export -- and the outputs seeds
  * int32[k], gains int64[k], num_seeds int32[1], coverage int64[1]; every
- * array must be device memory.  The call allocates nothing: its scratch is a
- * 64 MiB static device array inside the library, which every GPU that loads
- * the library holds until the process exits.  It needs
- * 4 n + theta / 8 + 33 KB bytes of it; larger instances get IM_ERR_CAPACITY.
- * The first call on a device looks up that array's device address (keep it
- * outside any stream capture).  All calls on a device share the one array,
+ * array must be memory of the current device (or managed memory); another
+ * GPU's memory gets IM_ERR_INVALID_ARG.  The arrays must form a valid
+ * instance: set_off and vtx_off start at 0, never decrease and end at the
+ * same total T; member ids lie in [0, n) and set ids in [0, theta).  A
+ * device pass checks this before the greedy runs and returns
+ * IM_ERR_INVALID_ARG (nothing written) otherwise.  The call allocates
+ * nothing: its scratch is a 64 MiB static device array inside the library,
+ * which every GPU that loads the library holds until the process exits.  It
+ * needs 4 n + theta / 8 + 33 KB bytes of it (rounded up to 256 bytes per
+ * part); larger instances get IM_ERR_CAPACITY.  Every call looks up that
+ * array's device address on the current device; the first call on a device
+ * also loads the library's kernels there (keep that first call outside any
+ * stream capture).  All calls on a device share the one array,
  * which keeps the previous call's contents: each call clears what must start
  * at zero, but calls that overlap on the GPU (other streams or threads) race
  * and must be serialised by the caller.  Synchronises the stream. */
@@ -306,16 +326,23 @@ im_status im_pool_reserve(im_pool *p, int64_t max_sets, int64_t max_entries);
  * ones the next theta ids.  SelectSeeds follows opts (NULL: plain greedy).
  * Outputs: seeds int32[k] (host or device), num_seeds, coverage of the final
  * pool, theta; info (optional) records the rounds.  Pools are allocated and
- * grown inside; IM_ERR_OOM if the RRR sets do not fit in device memory. */
+ * grown inside; IM_ERR_OOM if the RRR sets do not fit in device memory.
+ * With info->keep_pools nonzero on entry, the rounds' pool and the final pool
+ * are not destroyed but handed to the caller in info->round_pool and
+ * info->final_pool (the caller destroys them with im_pool_destroy); on an
+ * error no pool is handed over.  Otherwise both are NULL on return. */
 typedef struct {
     int32_t rounds;               /* martingale rounds run */
-    int32_t reserved;
+    int32_t keep_pools;           /* in: hand the pools to the caller */
     int64_t theta_rounds[64];     /* theta_i of each round */
+    int64_t cov_rounds[64];       /* coverage of round i's seeds on its theta_i sets */
     double lb;                    /* LB (1 if no round passed) */
     int64_t theta;                /* final theta */
     int64_t round_entries;        /* members in the rounds' pool */
     int64_t final_entries;        /* members in the final pool */
     int64_t examined;             /* edges examined by the final sampling */
+    im_pool *round_pool;          /* out (keep_pools): sample ids 0 .. theta_last - 1 */
+    im_pool *final_pool;          /* out (keep_pools): the next theta ids */
 } im_solve_info;
 
 im_status im_solve(const im_graph *g, im_model model, int32_t k, double eps, double ell,

@@ -6,10 +6,15 @@ counting, Sec. 3.2), SelectSeeds, CheckGoodness; then theta = ceil(lambda*/LB)
 fresh samples (ids after the rounds' ids) and a final SelectSeeds.  The
 formulas of Estimate / CheckGoodness / f are not in the paper (it defers to
 Tang et al. 2015 and Chen 2018); orc_imm_* in oracle.c writes them out.
-Parity unpinned: nothing in the paper fixes these numbers; the tests check
-the structure (doubling, stopping rule, final count), the guarantee the paper
-restates (seeds within 1 - 1/e - eps of the optimum, exact on tiny graphs) and
-the GPU's identity with this driver.
+The paper prints none of their values, so they are pinned from outside it
+(tests/test_oracle_imm.py): lambda' and lambda* against values worked out
+independently at the LiveJournal-shaped size; both against the failure
+budgets they are derived from (Chernoff / martingale tails, with the exact
+integer binomial); l' against the halved failure events; round counts and
+round thetas in exact rational arithmetic; CheckGoodness by a hand-worked
+case.  The tests also check the structure (doubling, stopping rule, final
+count) and the guarantee the paper restates (seeds within 1 - 1/e - eps of
+the optimum, exact on tiny graphs).
 """
 from __future__ import annotations
 

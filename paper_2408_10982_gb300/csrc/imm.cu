@@ -150,14 +150,17 @@ im_status im_solve(const im_graph *g, im_model model, int32_t k, double eps, dou
     while (((int64_t)1 << (rounds + 2)) <= n) ++rounds;
 
     im_status s = IM_OK;
-    im_pool *p = nullptr;
+    im_pool *p = nullptr, *kept = nullptr;
     void *res = nullptr;
     im_solve_info loc;
     std::memset(&loc, 0, sizeof(loc));
+    const bool keep = info && info->keep_pools;
+    loc.keep_pools = keep ? 1 : 0;
     double lb = 1.0;
     int64_t have = 0;
     auto fail = [&](im_status code) {
         if (p) im_pool_destroy(p);
+        if (kept) im_pool_destroy(kept);
         cudaFree(res);
         if (prev != g->device) cudaSetDevice(prev);
         return code;
@@ -187,6 +190,7 @@ im_status im_solve(const im_graph *g, im_model model, int32_t k, double eps, dou
         int64_t cov = 0;
         s = select_seeds(p, k, opts, d_seeds, d_gains, d_ns, d_cov, d_status, &cov, st);
         if (s != IM_OK) return fail(s);
+        if (loc.rounds <= 64) loc.cov_rounds[loc.rounds - 1] = cov;
         const double spread = dn * ((double)cov / (double)th);   // CheckGoodness
         if (spread >= (1.0 + e2) * x) {
             lb = spread / (1.0 + e2);
@@ -199,7 +203,8 @@ im_status im_solve(const im_graph *g, im_model model, int32_t k, double eps, dou
     loc.round_entries = p->total;
     // final phase: theta fresh samples, ids after the rounds' ids
     const double per = p->theta > 0 ? (double)p->total / (double)p->theta : 64.0;
-    im_pool_destroy(p);
+    if (keep) kept = p;
+    else im_pool_destroy(p);
     p = nullptr;
     if ((uint64_t)have + (uint64_t)theta > ((uint64_t)1 << 32) || theta >= ((int64_t)1 << 31)) {
         set_error("im_solve: theta exceeds the 2^31 sets one pool holds");
@@ -222,6 +227,11 @@ im_status im_solve(const im_graph *g, im_model model, int32_t k, double eps, dou
     if (theta_out) *theta_out = theta;
     loc.final_entries = p->total;
     loc.examined = p->examined;
+    if (keep) {
+        loc.round_pool = kept;
+        loc.final_pool = p;
+        kept = p = nullptr;
+    }
     if (info) *info = loc;
     return fail(IM_OK);
 }

@@ -150,6 +150,24 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
+// One cut point of the LT pick (see k_lt_guide), 32 bytes = one DRAM sector:
+// {running sum low word, high word, source u of the edge, u's first in-edge,
+//  u's in-degree, the edge's index within its in-list, 0, 0}.  Carrying u's
+// in-list lets the next step of a walk go straight to u's cut points.
+struct __align__(32) LtCut {
+    uint32_t cum_lo, cum_hi, src, src_eb;
+    uint32_t src_d, e, pad0, pad1;
+};
+
+__device__ __forceinline__ LtCut ld_lt_cut(const LtCut *p) {
+    LtCut c;
+    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(c.cum_lo), "=r"(c.cum_hi), "=r"(c.src), "=r"(c.src_eb), "=r"(c.src_d), "=r"(c.e),
+          "=r"(c.pad0), "=r"(c.pad1)
+        : "l"(p));
+    return c;
+}
+
 }  // namespace im
 
 // What a sampling kernel needs of one query: its graph and random stream.
@@ -161,7 +179,7 @@ struct QueryView {
     const uint4 *lt_vrec;
     const unsigned long long *lt_leaf;
     const unsigned long long *lt_tree;
-    const uint4 *lt_guide;
+    const im::LtCut *lt_guide;
     uint64_t seed;
     uint32_t n;
     uint32_t first;      // sample id of the query's first sample
@@ -181,7 +199,7 @@ struct im_graph {
     uint4 *lt_vrec;                  // [n] {edge offset, in-degree, tree offset, 0}
     unsigned long long *lt_leaf;     // [m]
     unsigned long long *lt_tree;     // [sum over vertices of the upper-level sizes]
-    uint4 *lt_guide;                 // [m] inverse-CDF cut points (see k_lt_guide)
+    im::LtCut *lt_guide;             // [m] inverse-CDF cut points (see k_lt_guide)
     // out-edge index, built on first im_spread: per source, the in-CSR ids
     // of its out-edges and their heads
     int64_t *out_off;                // [n+1]

@@ -8,8 +8,6 @@
 // im_max_k_cover_noalloc gives them the standard greedy over arrays they own:
 // its scratch space is this file's static device array, which every GPU that
 // loads the library holds until the process exits.
-#include <mutex>
-
 #include "internal.cuh"
 
 namespace im {
@@ -26,42 +24,55 @@ constexpr size_t kBestBytes = (size_t)kNoAllocMaxGrid * 8;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Resolve the device address of the static array once per device, with that
-// device current (the host-side symbol is only a stand-in, not an address).
+// Device address of the static array on the current device.  The host-side
+// symbol is only a stand-in, not an address; the runtime maps it per device
+// (and again in a new context after cudaDeviceReset), so it is looked up with
+// the device current on every call -- a lookup, not an allocation.  The first
+// call on a device also loads this module there.
 im_status scratch_address(void **out) {
-    int dev = 0;
-    IM_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("im_max_k_cover_noalloc: device ordinal out of range");
-        return IM_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e, "im_max_k_cover_noalloc: cudaGetSymbolAddress");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "im_max_k_cover_noalloc: cudaGetSymbolAddress");
+    *out = p;
     return IM_OK;
 }
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Every array handed to this entry point must be device memory: the kernel
-// reads and writes it directly.
-bool on_device(const void *p) {
+// Every array handed to this entry point must be memory the current device
+// can reach: its own device memory, or managed memory.  Another GPU's memory
+// is refused (without peer access the kernel would fault on it).
+bool on_device(const void *p, int dev) {
     if (!p) return true;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// The caller's arrays are checked before the greedy writes anything indexed by
+// them: both offset arrays start at 0 and never decrease, both end at the same
+// total T, every member id is below n and every set id below theta.  A
+// violation raises kDevBadInput (the call then returns IM_ERR_INVALID_ARG and
+// the greedy does not run).
+__global__ void k_noalloc_validate(const int64_t *set_off, const int32_t *members,
+                                   const int64_t *vtx_off, const int32_t *set_ids, int64_t n,
+                                   int64_t theta, int *status) {
+    const int64_t T = set_off[theta];
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (tid == 0 && (set_off[0] != 0 || vtx_off[0] != 0 || vtx_off[n] != T || T < 0))
+        raise_status(status, kDevBadInput);
+    if (T < 0 || vtx_off[n] != T) return;
+    bool bad = false;
+    for (int64_t i = tid; i < theta; i += stride) bad |= set_off[i + 1] < set_off[i];
+    for (int64_t v = tid; v < n; v += stride) bad |= vtx_off[v + 1] < vtx_off[v];
+    for (int64_t t = tid; t < T; t += stride)
+        bad |= (uint32_t)members[t] >= (uint64_t)n || (uint32_t)set_ids[t] >= (uint64_t)theta;
+    if (bad) raise_status(status, kDevBadInput);
 }
 
 }  // namespace
@@ -87,9 +98,13 @@ extern "C" im_status im_max_k_cover_noalloc(const int64_t *set_off, const int32_
                   "64 MiB array (use im_max_k_cover for larger instances)");
         return IM_ERR_CAPACITY;
     }
-    if (!on_device(set_off) || !on_device(members) || !on_device(vtx_off) || !on_device(set_ids) ||
-        !on_device(seeds) || !on_device(gains) || !on_device(num_seeds) || !on_device(coverage)) {
-        set_error("im_max_k_cover_noalloc: every array must be device memory");
+    int dev = 0;
+    IM_CUDA(cudaGetDevice(&dev));
+    if (!on_device(set_off, dev) || !on_device(members, dev) || !on_device(vtx_off, dev) ||
+        !on_device(set_ids, dev) || !on_device(seeds, dev) || !on_device(gains, dev) ||
+        !on_device(num_seeds, dev) || !on_device(coverage, dev)) {
+        set_error("im_max_k_cover_noalloc: every array must be memory of the current device "
+                  "(or managed memory)");
         return IM_ERR_INVALID_ARG;
     }
     void *base = nullptr;
@@ -102,13 +117,23 @@ extern "C" im_status im_max_k_cover_noalloc(const int64_t *set_off, const int32_
     IM_CUDA(cudaMemsetAsync(B, 0, kCtrlBytes, st));
     IM_CUDA(cudaMemsetAsync(num_seeds, 0, sizeof(int32_t), st));
     IM_CUDA(cudaMemsetAsync(coverage, 0, sizeof(int64_t), st));
+    int hstatus = 0;
+    k_noalloc_validate<<<num_sms() * 4, 256, 0, st>>>(set_off, members, vtx_off, set_ids, n, theta,
+                                                      d_status);
+    IM_CUDA(cudaGetLastError());
+    IM_CUDA(cudaMemcpyAsync(&hstatus, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IM_CUDA(cudaStreamSynchronize(st));
+    if (hstatus != kDevOk) {
+        set_error("im_max_k_cover_noalloc: offsets must start at 0, never decrease and end at "
+                  "the same total; member ids must be < n and set ids < theta");
+        return IM_ERR_INVALID_ARG;
+    }
     s = greedy_launch(n, theta, set_off, members, vtx_off, set_ids, k,
                       (int32_t *)(B + kCtrlBytes + kBestBytes),
                       (uint32_t *)(B + kCtrlBytes + kBestBytes + up256((size_t)n * 4)),
                       (unsigned long long *)(B + kCtrlBytes), kNoAllocMaxGrid, B, seeds, gains,
                       num_seeds, coverage, d_status, st);
     if (s != IM_OK) return s;
-    int hstatus = 0;
     IM_CUDA(cudaMemcpyAsync(&hstatus, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaStreamSynchronize(st));
     if (hstatus != kDevOk) return map_dev_status(hstatus, "im_max_k_cover_noalloc");

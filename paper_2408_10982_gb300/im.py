@@ -261,10 +261,12 @@ def im_max_k_cover_noalloc(set_off, members, vtx_off, set_ids, n: int, theta: in
 
 class SolveInfo(ctypes.Structure):
     """im_solve_info (see include/im.h)."""
-    _fields_ = [("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("theta_rounds", ctypes.c_int64 * 64), ("lb", ctypes.c_double),
-                ("theta", ctypes.c_int64), ("round_entries", ctypes.c_int64),
-                ("final_entries", ctypes.c_int64), ("examined", ctypes.c_int64)]
+    _fields_ = [("rounds", ctypes.c_int32), ("keep_pools", ctypes.c_int32),
+                ("theta_rounds", ctypes.c_int64 * 64), ("cov_rounds", ctypes.c_int64 * 64),
+                ("lb", ctypes.c_double), ("theta", ctypes.c_int64),
+                ("round_entries", ctypes.c_int64), ("final_entries", ctypes.c_int64),
+                ("examined", ctypes.c_int64), ("round_pool", ctypes.c_void_p),
+                ("final_pool", ctypes.c_void_p)]
 
 
 class Query(ctypes.Structure):
@@ -402,13 +404,16 @@ def im_pool_reserve(p, max_sets: int, max_entries: int):
 
 
 def im_solve(g, model: int, k: int, eps: float, ell: float, seed: int,
-             opts: CoverOpts | None = None, stream=None):
-    """IMM (Alg. 1) on the device path: returns (seeds, coverage, theta, info)."""
+             opts: CoverOpts | None = None, stream=None, keep_pools: bool = False):
+    """IMM (Alg. 1) on the device path: returns (seeds, coverage, theta, info).
+    With keep_pools, info.round_pool / info.final_pool are pool handles the
+    caller must destroy (im_pool_destroy)."""
     seeds = np.zeros(k, np.int32)
     ns = ctypes.c_int32()
     cov = ctypes.c_int64()
     theta = ctypes.c_int64()
     info = SolveInfo()
+    info.keep_pools = 1 if keep_pools else 0
     _check(lib().im_solve(g, model, k, eps, ell, seed,
                           None if opts is None else ctypes.byref(opts), seeds.ctypes.data,
                           ctypes.byref(ns), ctypes.byref(cov), ctypes.byref(theta),

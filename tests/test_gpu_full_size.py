@@ -207,3 +207,75 @@ def test_rmat20_lt_spread_of_greedy_seeds(im):
     assert np.array_equal(act, ra)
     pool.close()
     G.close()
+
+
+def _pool_sets(im, handle, n):
+    theta, total, _ = im.im_pool_info(handle)
+    set_off = np.zeros(theta + 1, np.int64)
+    members = np.zeros(max(total, 1), np.int32)
+    im.im_pool_export(handle, set_off, members)
+    return set_off, members[:total]
+
+
+def test_imm_at_the_livejournal_size(im):
+    """IMM (Alg. 1) as configured for the LiveJournal-shaped graph: eps = 0.13,
+    l = 1, k = 200, IC weighted cascade (4,847,571 vertices, 69,000,000 edges).
+    Against the oracle: every round's theta_i, each round's CheckGoodness
+    decision and LB from the coverage it reached, the final theta = ceil(lambda*
+    / LB); sets at the start and the end of the rounds' pool and of the final
+    pool (the final pool's ids continue after the rounds'), each computed by
+    the oracle; and, on the whole final pool, that the reported coverage is the
+    number of sets that contain a seed and that the first seed is a vertex in
+    the most sets."""
+    import ctypes
+    from oracle import imm as OI
+    g = inputs.graph_livejournal_like_both(42)["wc"]
+    n, k, eps, ell, seed = g.n, 200, 0.13, 1.0, 42
+    G = im.Graph(g)
+    seeds, cov, theta, info = im.im_solve(G.handle, im.IM_IC, k, eps, ell, seed, keep_pools=True)
+    try:
+        c = OI.constants(n, k, eps, ell)
+        lib = OI._imm_lib()
+        assert 1 <= info.rounds <= c["rounds"]
+        lb = 1.0
+        for i in range(1, info.rounds + 1):
+            th = int(lib.orc_imm_round_theta(c["lambda_prime"], n, i))
+            assert info.theta_rounds[i - 1] == th
+            out = ctypes.c_double(0.0)
+            passed = lib.orc_imm_check(n, int(info.cov_rounds[i - 1]), th, i, c["eps2"],
+                                       ctypes.byref(out))
+            assert passed == (1 if i == info.rounds and info.lb != 1.0 else 0), i
+            if passed:
+                lb = out.value
+        assert info.lb == lb
+        assert theta == info.theta == int(lib.orc_imm_final_theta(c["lambda_star"], lb))
+        last = int(info.theta_rounds[info.rounds - 1])
+
+        # the rounds' pool holds ids 0 .. last-1, the final pool the next theta ids
+        r_off, r_mem = _pool_sets(im, info.round_pool, n)
+        f_off, f_mem = _pool_sets(im, info.final_pool, n)
+        assert r_off.size - 1 == last and f_off.size - 1 == theta
+        assert r_mem.size == info.round_entries and f_mem.size == info.final_entries
+        for off, mem, first, ids in ((r_off, r_mem, 0, [(0, 768), (last - 256, 256)]),
+                                     (f_off, f_mem, last, [(0, 768), (theta - 256, 256)])):
+            for a, cnt in ids:
+                ref = O.sample(O.IC, g, seed, first + a, cnt)
+                got_off = off[a:a + cnt + 1] - off[a]
+                assert np.array_equal(got_off, ref.set_off), (first, a)
+                assert np.array_equal(mem[off[a]:off[a + cnt]], ref.members), (first, a)
+
+        # the final answer, on the whole final pool
+        assert 1 <= len(seeds) <= k and len(set(seeds.tolist())) == len(seeds)
+        is_seed = np.zeros(n, bool)
+        is_seed[seeds] = True
+        set_of = np.repeat(np.arange(theta), np.diff(f_off))
+        hit = np.zeros(theta, bool)
+        hit[set_of[is_seed[f_mem]]] = True
+        assert cov == int(hit.sum())
+        deg = np.bincount(f_mem, minlength=n)
+        assert deg[seeds[0]] == deg.max() and seeds[0] == int(np.argmax(deg))
+    finally:
+        for h in (info.round_pool, info.final_pool):
+            if h:
+                im.im_pool_destroy(h)
+        G.close()

@@ -1,6 +1,10 @@
-"""Structure of the oracle's IMM driver (Alg. 1).  The formulas themselves are
-not in the paper (it defers them to Tang et al. 2015): parity unpinned; these
-tests check the structure Alg. 1 fixes."""
+"""The oracle's IMM driver (Alg. 1).  The paper defers the formulas of Estimate,
+CheckGoodness and f(LB) to Tang et al. (2015); they are pinned here by values
+computed independently at the LiveJournal-shaped size, by the failure budgets
+they are derived from (Chernoff and martingale tails, checked with the exact
+integer binomial), by exact rational checks of the round counts, and by a
+hand-worked CheckGoodness; the structure Alg. 1 fixes (doubling rounds, the
+stopping rule, the final count) and the restated guarantee are checked too."""
 import itertools
 import math
 
@@ -49,3 +53,102 @@ def test_imm_seeds_meet_the_papers_guarantee(orc, n, m, p, gseed):
     opt = max(brute.ic_spread_exact(g, list(S)) for S in itertools.combinations(range(g.n), k))
     got = brute.ic_spread_exact(g, [int(v) for v in r.seeds])
     assert float(got) >= (1 - 1 / math.e - eps) * float(opt)
+
+
+# ---------------------------------------------------------------------------
+# Pins of the IMM formulas themselves (Tang et al. 2015, the work Alg. 1 defers
+# to), each fixed by something other than the oracle's own expressions.
+# ---------------------------------------------------------------------------
+
+def test_lambdas_at_the_livejournal_size_match_values_computed_elsewhere(orc):
+    """lambda' ~ 6.80e11 and lambda* ~ 9.25e11 at n = 4,847,571, k = 200,
+    eps = 0.13, l = 1: values worked out independently of this code when the
+    workload was specified, to three significant figures.  log2 for ln in
+    ln C(n,k) (9.79e11), l for l' in lambda* (9.22e11), eps for e' or a dropped
+    factor 2 each change the printed digits."""
+    c = imm.constants(4847571, 200, 0.13, 1.0)
+    assert round(c["lambda_prime"] / 1e11, 2) == 6.80
+    assert round(c["lambda_star"] / 1e11, 2) == 9.25
+
+
+CASES = [(4847571, 200, 0.13, 1.0), (1 << 20, 100, 0.077, 1.0), (1000, 5, 0.5, 1.0),
+         (100, 1, 0.3, 2.0), (5000, 50, 0.1, 1.5)]
+
+
+@pytest.mark.parametrize("n,k,eps,ell", CASES)
+def test_l_prime_halves_each_failure_event(orc, n, k, eps, ell):
+    """IMM fails through two events (a round certifies a too-large LB; the final
+    pool picks a bad set), so l is raised to l' with n^-l' = n^-l / 2^l: two
+    events of probability n^-l' stay within n^-l for l >= 1."""
+    c = imm.constants(n, k, eps, ell)
+    assert math.isclose(c["ell2"] * math.log(n), ell * math.log(n) + ell * math.log(2),
+                        rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("n,k,eps,ell", CASES)
+def test_lambda_star_spends_exactly_the_final_failure_budget(orc, n, k, eps, ell):
+    """theta = lambda*/OPT samples must make both Chernoff tails of the final
+    phase equal to n^-l'/2: the lower tail of the optimal set,
+    exp(-e1^2 lambda* / (2n)), and the union over the C(n,k) seed sets whose
+    spread is below (1 - 1/e - eps) OPT of the upper tail
+    exp(-(eps - (1-1/e) e1)^2 lambda* / (2 (1-1/e) n)).  The first equation
+    fixes e1; the second must then hold, and only the right lambda* does it.
+    ln C(n,k) is computed from the exact integer binomial, not lgamma."""
+    c = imm.constants(n, k, eps, ell)
+    L = c["lambda_star"]
+    q = 1 - 1 / math.e
+    budget = c["ell2"] * math.log(n) + math.log(2)            # -ln(n^-l' / 2)
+    ln_c = math.log(math.comb(n, k))
+    e1 = math.sqrt(2 * n * budget / L)
+    assert 0 < q * e1 < eps
+    assert math.isclose(ln_c - (eps - q * e1) ** 2 * L / (2 * q * n), -budget, rel_tol=1e-9)
+
+
+@pytest.mark.parametrize("n,k,eps,ell", CASES)
+def test_lambda_prime_spends_exactly_the_round_failure_budget(orc, n, k, eps, ell):
+    """A round with theta_i = lambda'/x_i samples certifies LB = x_i falsely
+    (OPT < x_i) with probability at most exp(-e'^2 lambda' / ((2 + 2e'/3) n))
+    per seed set (the martingale tail of Tang et al.); a union over C(n,k) sets
+    and log2 n rounds must equal n^-l'.  e' = sqrt(2) eps."""
+    c = imm.constants(n, k, eps, ell)
+    e2 = math.sqrt(2) * eps
+    assert math.isclose(c["eps2"], e2, rel_tol=1e-15)
+    ln_c = math.log(math.comb(n, k))
+    lhs = ln_c + math.log(math.log2(n)) - e2 ** 2 * c["lambda_prime"] / ((2 + 2 * e2 / 3) * n)
+    assert math.isclose(lhs, -c["ell2"] * math.log(n), rel_tol=1e-9)
+
+
+@pytest.mark.parametrize("n,rounds", [(4, 1), (7, 1), (8, 2), ((1 << 20) - 1, 18), (1 << 20, 19),
+                                      ((1 << 20) + 1, 19), (4847571, 21)])
+def test_round_count_is_floor_log2_n_minus_one(orc, n, rounds):
+    assert imm.constants(n, 1, 0.5, 1.0)["rounds"] == rounds
+
+
+@pytest.mark.parametrize("n,i", [(4847571, 1), (4847571, 4), (1000, 3), (1 << 20, 19)])
+def test_round_theta_is_the_least_integer_reaching_lambda_prime(orc, n, i):
+    """theta_i = ceil(lambda' / x_i), x_i = n / 2^i: checked in exact rational
+    arithmetic (theta_i x_i >= lambda' > (theta_i - 1) x_i)."""
+    from fractions import Fraction
+    lib = imm._imm_lib()
+    lam1 = imm.constants(n, 10, 0.2, 1.0)["lambda_prime"]
+    th = int(lib.orc_imm_round_theta(lam1, n, i))
+    x = Fraction(n, 2 ** i)
+    assert th * x >= Fraction(lam1) > (th - 1) * x
+
+
+def test_check_goodness_hand_worked(orc):
+    """CheckGoodness with e' = 1 (exact in binary): n = 1000, round i = 3, so
+    x = 125 and the bar is (1 + e') x = 250.  theta_i = 100 sets, coverage 25:
+    n F = 1000 * 25 / 100 = 250 >= 250 passes (the comparison is >=) with
+    LB = 250 / 2 = 125; coverage 24 gives 240 < 250 and fails."""
+    import ctypes
+    lib = imm._imm_lib()
+    lb = ctypes.c_double(-1.0)
+    assert lib.orc_imm_check(1000, 25, 100, 3, 1.0, ctypes.byref(lb)) == 1
+    assert lb.value == 125.0
+    lb = ctypes.c_double(-1.0)
+    assert lib.orc_imm_check(1000, 24, 100, 3, 1.0, ctypes.byref(lb)) == 0
+    assert lb.value == -1.0
+    # and the final count: theta = ceil(lambda* / LB)
+    assert lib.orc_imm_final_theta(1000.0, 125.0) == 8
+    assert lib.orc_imm_final_theta(1000.5, 125.0) == 9
