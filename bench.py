@@ -15,7 +15,7 @@ theta = 4,194,304, k = 100, delta = 0.077.
 
 `value` is RRR edges examined per second over whole steps (the in-edges a
 cumulative-weight scan would decide over, identical to the oracle's count;
-the GPU walk does not read them -- one 32-byte cut point decides each step --
+the GPU walk does not read them -- one 16-byte cut point decides each step --
 so `walk_steps_per_s` and `roofline` give its real rate), with the graph
 resident in HBM.  `e2e` is the same metric through the C ABI
 from pinned host arrays: graph upload, LT index build, sampling, both covers
@@ -345,9 +345,9 @@ def run_ours(args):
                 "traffic_over_alg": round(traffic / sbytes, 3) if traffic else None,
                 "alg_bytes_per_launch": sbytes,
                 "alg_bytes": "the walk kernel's own loads and stores, counted by the kernel: "
-                             "32 B cut point per step (+ search probes and the source's "
-                             "vertex record when the draw lies past it), 4 B per member, "
-                             "28 B per set",
+                             "per step a 16 B vertex record and a 16 B cut point (+ 8 B per "
+                             "search probe when the draw lies past it), 4 B per member, "
+                             "12 B per set",
                 "launch_ms": round(samp_launch_ms, 4),
                 "walk_steps_per_launch": total,
                 "dominant_kernel": dominant,
@@ -363,7 +363,7 @@ def run_ours(args):
                        "tuned": {k2: v for k2, v in tuned.items() if k2 != "ms"}},
             "value_note": "examined edges = the in-edges a cumulative-weight scan would "
                           "decide over (the oracle's count, identical); the GPU walk does "
-                          "not read them: one 32-byte cut point decides each step",
+                          "not read them: one 16-byte cut point decides each step",
             "sets_per_s": world * theta / (ms_step / 1000.0),
             "entries_per_s": world * total / (ms_step / 1000.0),
             "walk_steps_per_s": world * total / (ms_step / 1000.0),
@@ -373,6 +373,7 @@ def run_ours(args):
             "gpu_launches": launches, "roofline": roofline, "clocks": clk}
 
     pool_stats = cover_stats(im, pool, g.n, theta, K, opts_rg)
+    cover_paths = bench_cover_paths(im, pool, opts_rg) if not args.no_extras else None
     spread = bench_spread(im, torch, G, pool, g.n, theta) if not args.no_extras else None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["bit_exact"], line["cpu_baseline"] = cpu_baseline_and_check(g, pool, first)
@@ -383,6 +384,8 @@ def run_ours(args):
     line["kernels"] = kernel_rooflines(im, pool_stats, per, hbm)
     if spread:
         line["spread"] = spread
+    if cover_paths:
+        line["cover_paths"] = cover_paths
     if not args.no_extras:
         line["batched"] = bench_batched(im, torch)
         line["served"] = bench_served(im, torch, args.served_orkut)
@@ -487,6 +490,43 @@ def cover_stats(im, pool, n, theta, k, opts_rg):
     return {"T": int(set_off[-1]), "n": n, "theta": theta, "k": k, "s_seed": s_seed,
             "covered": int(covered.size), "r_covered": int(np.sum(sizes[covered])),
             "rg_eval": int(st[:PARTS, 4].sum()), "rg_cover": int(st[:PARTS, 5].sum())}
+
+
+def bench_cover_paths(im, pool, opts_rg):
+    """The other max-k-cover paths on the step's pool (after the timed region):
+    the standard greedy by its counts-decrement kernel and by the lazy kernel
+    (Alg. 2) at two widths -- the same seeds -- and RandGreedi with Alg. 4's
+    non-streaming global step next to the streaming one.  Kernel time per
+    cover (CUDA events, mean of 3), coverage, and the lazy kernel's counters."""
+    paths = [("greedy_counts", 0, None),
+             ("greedy_lazy_w8", 8, im.cover_opts(im.IM_GREEDY_LAZY)),
+             ("greedy_lazy_w32", 32, im.cover_opts(im.IM_GREEDY_LAZY)),
+             ("randgreedi_stream", 0, opts_rg),
+             ("randgreedi_naive", 16, im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED,
+                                                    fused=False, aggregator=im.IM_AGG_GREEDY))]
+    out, ref = {}, None
+    for name, width, opts in paths:
+        im.im_tune_set(im.IM_TUNE_GREEDY_EVALS, width)
+        pool.cover(K, opts)                              # warm-up
+        im.im_profile_reset()
+        im.im_profile_enable(True)
+        for _ in range(3):
+            c = pool.cover(K, opts)
+        im.im_profile_enable(False)
+        prof = im.im_profile_read()
+        ms = sum(v[1] for v in prof.values()) / 3
+        e = {"kernel_ms": round(ms, 3), "coverage": int(c.coverage), "seeds": int(len(c.seeds)),
+             "kernels": {k2: round(v[1] / 3, 3) for k2, v in sorted(prof.items())}}
+        if name == "greedy_counts":
+            ref = c
+        elif name.startswith("greedy_lazy"):
+            e["same_as_counts"] = bool(c.seeds.tolist() == ref.seeds.tolist() and
+                                       c.coverage == ref.coverage)
+        if "lazy" in name or "naive" in name:
+            e["lazy_stats"] = im.im_greedy_stats(pool.handle)
+        out[name] = e
+    im.im_tune_set(im.IM_TUNE_GREEDY_EVALS, 0)
+    return out
 
 
 def kernel_rooflines(im, cs, per, hbm):

@@ -53,11 +53,19 @@ typedef enum {
 
 typedef enum { IM_IC = 0, IM_LT = 1 } im_model;
 
-typedef enum { IM_GREEDY_PLAIN = 0, IM_RANDGREEDI = 1 } im_cover_algo;
+typedef enum { IM_GREEDY_PLAIN = 0, IM_RANDGREEDI = 1, IM_GREEDY_LAZY = 2 } im_cover_algo;
+
+/* RandGreedi's global step (Alg. 4, line 5). */
+typedef enum { IM_AGG_STREAM = 0, IM_AGG_GREEDY = 1 } im_aggregator;
 
 /* Options of im_max_k_cover.
- *   algo            IM_GREEDY_PLAIN: standard greedy over all of V (Sec. 3.2).
+ *   algo            IM_GREEDY_PLAIN: standard greedy over all of V (Sec. 3.2);
+ *                   the kernel that runs it is IM_TUNE_GREEDY_EVALS' choice.
  *                   IM_RANDGREEDI: Alg. 4 with Alg. 5 aggregation.
+ *                   IM_GREEDY_LAZY: the lazy greedy of Alg. 2 over all of V
+ *                   (re-evaluates only candidates whose stale gain bound is
+ *                   on top); with ties to the smallest id its seeds, gains and
+ *                   coverage equal IM_GREEDY_PLAIN's.
  *   partitions      number of random vertex parts m (RandGreedi), 1..4096.
  *   alpha_num/den   truncation alpha = num/den in (0, 1]: every partition
  *                   computes k local seeds and streams its first
@@ -71,7 +79,15 @@ typedef enum { IM_GREEDY_PLAIN = 0, IM_RANDGREEDI = 1 } im_cover_algo;
  *                   global memory); 0 runs them as two launches, the second
  *                   keeping each bucket's bitmap in the shared memory of a
  *                   thread-block cluster (see IM_TUNE_RG_CLUSTER).  Results
- *                   are identical. */
+ *                   are identical.
+ *   aggregator      RandGreedi only: IM_AGG_STREAM (0) aggregates with the
+ *                   streaming buckets of Alg. 5 (Sec. 3.3); IM_AGG_GREEDY (1)
+ *                   is Alg. 4's global step as written: the lazy greedy of
+ *                   Alg. 2 over the union of the gathered local seeds (the
+ *                   first max(1, ceil(alpha k)) of every part), after all
+ *                   local solutions are complete.  Its result is reported as
+ *                   bucket 0 (B = 1, threshold 0) by im_randgreedi_details;
+ *                   fused and delta are ignored. */
 typedef struct {
     int32_t algo;
     int32_t partitions;
@@ -80,7 +96,7 @@ typedef struct {
     double delta;
     uint64_t partition_seed;
     int32_t fused;
-    int32_t reserved;
+    int32_t aggregator;
 } im_cover_opts;
 
 typedef struct im_graph im_graph;   /* device-resident graph, library-owned */
@@ -187,11 +203,11 @@ im_status im_randgreedi_details(const im_pool *p, int32_t *P_out, int32_t *B_out
  * on-chip and not counted):
  *   IC: per member 16 (its in-CSR offset pair) + 4 (member write),
  *       per examined edge 8 (source id + weight), per set 8 (offset);
- *   LT, one walk per thread (the default): per set 8 (offset) + 16 (the
- *       root's vertex record) + 4 (root write); per step at a vertex with
- *       in-degree d > 0: 32 (one cut point); when the draw lies past the cut
- *       point's edge, 8 per binary-search probe actually made, plus 8 + 16
- *       (the picked leaf and its source's vertex record); 4 per member added.
+ *   LT, one walk per thread (the default): per set 8 (offset) + 4 (root
+ *       write); per step 16 (the vertex record), + 16 (one cut point) when the
+ *       in-degree is > 0; when the draw lies past the cut point's edge, 8 per
+ *       binary-search probe actually made + 8 (the picked leaf); 4 per member
+ *       added.
  *   LT, G lanes per walk: per walk step at a vertex of in-degree d: 16
  *       (offset pair) + 8 (floor(log2 d) + 1) when d > 0 (search of the
  *       cumulative weights) + 4 when an edge is picked (its source) + 4
@@ -224,12 +240,19 @@ im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
  *                       on hub vertices; the order of set ids inside an S(v)
  *                       is unspecified in every case.
  *   IM_TUNE_RG_EVALS    RandGreedi local greedy: candidates re-evaluated per
- *                       round, 1, 2 (default), 4 or 8. */
+ *                       round, 1, 2 (default), 4 or 8.
+ *   IM_TUNE_GREEDY_EVALS  the kernel of IM_GREEDY_PLAIN: 0 (default) runs the
+ *                       standard greedy that decrements the gain of every
+ *                       member of every newly covered set; 1, 2, 4, 8, 16 or
+ *                       32 runs the lazy greedy of Alg. 2 with that many
+ *                       candidates re-evaluated at once (also the width
+ *                       IM_GREEDY_LAZY uses; 0 means 16 there). */
 typedef enum {
     IM_TUNE_LT_GROUP = 0,
     IM_TUNE_RG_CLUSTER = 1,
     IM_TUNE_INDEX_REPLICAS = 2,
-    IM_TUNE_RG_EVALS = 3
+    IM_TUNE_RG_EVALS = 3,
+    IM_TUNE_GREEDY_EVALS = 4
 } im_tune_knob;
 im_status im_tune_set(int32_t knob, int64_t value);
 im_status im_tune_get(int32_t knob, int64_t *value);
@@ -279,6 +302,12 @@ im_status im_profile_read(int32_t max_entries, char *names, int64_t *launches, d
  *   covered.  Row P + b (bucket b): start ns, end ns, elements evaluated,
  *   elements accepted, entries scanned, ns spent waiting for the stream. */
 im_status im_randgreedi_stats(const im_pool *p, int64_t *stats, void *stream);
+
+/* Diagnostics of the pool's last lazy-greedy cover (IM_GREEDY_LAZY, or
+ * IM_GREEDY_PLAIN with IM_TUNE_GREEDY_EVALS > 0): int64[4] = rounds, candidate
+ * evaluations, covering-subset entries scanned by them, and builds of the
+ * sorted bound list.  Zero if no such cover ran. */
+im_status im_greedy_stats(const im_pool *p, int64_t *stats);
 
 /* Standard greedy max-k-cover (same result as im_max_k_cover with
  * IM_GREEDY_PLAIN) for callers that cannot let the library allocate device

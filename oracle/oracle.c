@@ -270,6 +270,85 @@ int orc_greedy(int64_t n, int64_t theta, const int64_t *set_off, const int32_t *
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Lazy greedy max-k-cover (Alg. 2): a max heap Q of (key, vertex) built    */
+/* from |S(v)|; pop the top v, compute its marginal gain against the sets   */
+/* covered so far; take v when the gain is at least the new top's key, else */
+/* push v back with its gain as the key.  Keys order by (value, smaller id  */
+/* first), so "at least" with equal values means v's id is the smaller one  */
+/* (the tie rule of the standard greedy).  A popped gain of 0 that would be */
+/* taken ends the selection (zero-gain stop).  Candidates as in orc_greedy. */
+/* Returns 0, or -1 on allocation failure.                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct { int64_t key; int32_t v; } orc_hent;
+
+static int orc_hent_above(orc_hent a, orc_hent b) {   /* a ranks above b */
+    return a.key > b.key || (a.key == b.key && a.v < b.v);
+}
+
+static void orc_heap_push(orc_hent *h, int64_t *len, orc_hent x) {
+    int64_t i = (*len)++;
+    while (i > 0) {
+        int64_t parent = (i - 1) / 2;
+        if (!orc_hent_above(x, h[parent])) break;
+        h[i] = h[parent];
+        i = parent;
+    }
+    h[i] = x;
+}
+
+static orc_hent orc_heap_pop(orc_hent *h, int64_t *len) {
+    orc_hent top = h[0], last = h[--(*len)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= *len) break;
+        if (c + 1 < *len && orc_hent_above(h[c + 1], h[c])) ++c;
+        if (!orc_hent_above(h[c], last)) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*len > 0) h[i] = last;
+    return top;
+}
+
+int orc_lazy_greedy(int64_t n, int64_t theta, const int64_t *vtx_off, const int32_t *set_ids,
+                    int32_t k, const int32_t *cand, int64_t ncand, int32_t *seeds,
+                    int64_t *gains, int32_t *nseeds, int64_t *coverage) {
+    int64_t span = cand ? ncand : n, len = 0;
+    orc_hent *Q = (orc_hent *)malloc((size_t)(span > 0 ? span : 1) * sizeof(orc_hent));
+    uint8_t *covered = (uint8_t *)calloc((size_t)theta + 1, 1);
+    if (!Q || !covered) { free(Q); free(covered); return -1; }
+    for (int64_t c = 0; c < span; ++c) {
+        int32_t v = cand ? cand[c] : (int32_t)c;
+        orc_hent x = { vtx_off[v + 1] - vtx_off[v], v };
+        orc_heap_push(Q, &len, x);
+    }
+    int32_t picked = 0;
+    int64_t cov = 0;
+    while (picked < k && len > 0) {
+        orc_hent top = orc_heap_pop(Q, &len);
+        int64_t gain = 0;
+        for (int64_t t = vtx_off[top.v]; t < vtx_off[top.v + 1]; ++t) gain += !covered[set_ids[t]];
+        orc_hent now = { gain, top.v };
+        if (len == 0 || !orc_hent_above(Q[0], now)) {
+            if (gain == 0) break;              /* every remaining gain is zero */
+            seeds[picked] = top.v;
+            gains[picked] = gain;
+            ++picked;
+            cov += gain;
+            for (int64_t t = vtx_off[top.v]; t < vtx_off[top.v + 1]; ++t) covered[set_ids[t]] = 1;
+        } else {
+            orc_heap_push(Q, &len, now);
+        }
+    }
+    *nseeds = picked;
+    *coverage = cov;
+    free(Q);
+    free(covered);
+    return 0;
+}
+
 /* Number of buckets B = ceil(log_{1+delta}(u/l)) with u/l = k (Alg. 5;        */
 /* u/l = k per the runtime analysis of Sec. 3.4), taken as the least b >= 1    */
 /* with (1+delta)^b >= k, the power formed by repeated multiplication.        */
@@ -327,6 +406,8 @@ int orc_stream_buckets(int64_t theta, const int64_t *vtx_off, const int32_t *set
 /* (Alg. 3 partition, Alg. 4 local greedy + final compare, Alg. 5 stream,   */
 /* Sec. 3.3.2 truncation: each partition computes all k local seeds and     */
 /* streams only its first `trunc`).  The partitions run one after another. */
+/* naive != 0: Alg. 4's global step is the lazy greedy over the gathered    */
+/* seeds instead of the streaming buckets (B = 1).                          */
 /* Outputs:                                                                 */
 /*   local_seeds/local_gains [P*k], local_n [P], local_cov [P]              */
 /*   B, thr [B], bucket_cov [B], bucket_n [B], bucket_seeds [B*k],          */
@@ -336,7 +417,7 @@ int orc_stream_buckets(int64_t theta, const int64_t *vtx_off, const int32_t *set
 /* ------------------------------------------------------------------------ */
 int orc_randgreedi(int64_t n, int64_t theta, const int64_t *set_off, const int32_t *members,
                    const int64_t *vtx_off, const int32_t *set_ids, int32_t k, int32_t P,
-                   uint64_t pseed, int32_t trunc, double delta,
+                   uint64_t pseed, int32_t trunc, double delta, int32_t naive,
                    int32_t *local_seeds, int64_t *local_gains, int32_t *local_n,
                    int64_t *local_cov, int64_t *thr, int64_t *bucket_cov, int32_t *bucket_n,
                    int32_t *bucket_seeds, int64_t *bucket_gains, int32_t *chosen,
@@ -364,15 +445,27 @@ int orc_randgreedi(int64_t n, int64_t theta, const int64_t *set_off, const int32
         for (int32_t p = 0; p < P; ++p)
             if (j < local_n[p]) stream[ns++] = local_seeds[(int64_t)p * k + j];
 
-    /* l = largest single covering subset; u = k l */
-    int64_t l = 0;
-    for (int64_t v = 0; v < n; ++v)
-        if (vtx_off[v + 1] - vtx_off[v] > l) l = vtx_off[v + 1] - vtx_off[v];
-    int32_t B = orc_num_buckets(k, delta);
-    orc_bucket_thresholds(l, k, delta, B, thr);
-    if (orc_stream_buckets(theta, vtx_off, set_ids, stream, ns, k, B, thr, bucket_cov,
-                           bucket_n, bucket_seeds, bucket_gains)) {
-        free(part); free(allowed); free(stream); return -1;
+    int32_t B;
+    if (naive) {
+        /* Alg. 4 as written: the lazy greedy (Alg. 2) over the union of the   */
+        /* gathered local seeds, reported as bucket 0 with threshold 0        */
+        B = 1;
+        thr[0] = 0;
+        if (orc_lazy_greedy(n, theta, vtx_off, set_ids, k, stream, ns, bucket_seeds,
+                            bucket_gains, &bucket_n[0], &bucket_cov[0])) {
+            free(part); free(allowed); free(stream); return -1;
+        }
+    } else {
+        /* l = largest single covering subset; u = k l */
+        int64_t l = 0;
+        for (int64_t v = 0; v < n; ++v)
+            if (vtx_off[v + 1] - vtx_off[v] > l) l = vtx_off[v + 1] - vtx_off[v];
+        B = orc_num_buckets(k, delta);
+        orc_bucket_thresholds(l, k, delta, B, thr);
+        if (orc_stream_buckets(theta, vtx_off, set_ids, stream, ns, k, B, thr, bucket_cov,
+                               bucket_n, bucket_seeds, bucket_gains)) {
+            free(part); free(allowed); free(stream); return -1;
+        }
     }
 
     /* best bucket (ties: smallest b) vs best local solution (ties: smallest p) */

@@ -14,9 +14,14 @@ Parity status (what pins each function, see tests/test_oracle_*.py):
   invert        dict-of-sets transpose
   greedy        from-scratch marginal-gain greedy with Python sets;
                 (1-1/e) and truncated (1-(1-1/k)^j) bounds vs optimal cover
+  lazy_greedy   equals the standard greedy (submodularity: stale gains are
+                upper bounds) on random and tie-heavy instances; a
+                hand-worked heap trace of Alg. 2
   partition     chi-square balance; determinism
   stream        (1/2)/(1+delta) bound vs the optimal cover of the stream
-  randgreedi    locals equal greedy on the induced instance; final rule
+  randgreedi    locals equal greedy on the induced instance; final rule;
+                naive global step equals the standard greedy over the
+                gathered seeds
 """
 from __future__ import annotations
 
@@ -81,7 +86,9 @@ def _lib():
         lib.orc_spread.argtypes = [ctypes.c_int, i64, vp, vp, vp, u64, u64, u64, vp, i32, vp, vp]
         lib.orc_randgreedi.restype = ctypes.c_int
         lib.orc_randgreedi.argtypes = [i64, i64, vp, vp, vp, vp, i32, i32, u64, i32,
-                                       ctypes.c_double] + [vp] * 14
+                                       ctypes.c_double, i32] + [vp] * 14
+        lib.orc_lazy_greedy.restype = ctypes.c_int
+        lib.orc_lazy_greedy.argtypes = [i64, i64, vp, vp, i32, vp, i64, vp, vp, vp, vp]
         _LIB = lib
     return _LIB
 
@@ -202,6 +209,25 @@ def greedy(n: int, pool: Pool, inv, k: int, cand: np.ndarray | None = None) -> C
     return Cover(seeds[: ns.value].copy(), gains[: ns.value].copy(), int(cov.value))
 
 
+def lazy_greedy(n: int, pool: Pool, inv, k: int, cand: np.ndarray | None = None) -> Cover:
+    """Lazy greedy max-k-cover of Alg. 2 (a max heap of stale gains; ties ->
+    smallest id, stops at zero gain)."""
+    vtx_off, set_ids = inv
+    seeds = np.zeros(max(k, 1), dtype=np.int32)
+    gains = np.zeros(max(k, 1), dtype=np.int64)
+    ns = ctypes.c_int32()
+    cov = ctypes.c_int64()
+    cand_a = None if cand is None else _c(cand, np.int32)
+    if cand_a is not None and cand_a.size == 0:
+        return Cover(np.zeros(0, np.int32), np.zeros(0, np.int64), 0)
+    rc = _lib().orc_lazy_greedy(n, pool.theta, _p(vtx_off), _p(set_ids), k, _p(cand_a),
+                                0 if cand_a is None else cand_a.size, _p(seeds), _p(gains),
+                                ctypes.byref(ns), ctypes.byref(cov))
+    if rc:
+        raise MemoryError
+    return Cover(seeds[: ns.value].copy(), gains[: ns.value].copy(), int(cov.value))
+
+
 def num_buckets(k: int, delta: float) -> int:
     return int(_lib().orc_num_buckets(k, delta))
 
@@ -257,9 +283,12 @@ def trunc_count(k: int, alpha_num: int, alpha_den: int) -> int:
 
 
 def randgreedi(n: int, pool: Pool, inv, k: int, P: int, pseed: int, trunc: int,
-               delta: float) -> RandGreedi:
+               delta: float, naive: bool = False) -> RandGreedi:
+    """Alg. 3 + Alg. 4 with the streaming aggregator of Alg. 5 and truncation
+    (Sec. 3.3.2); naive=True: Alg. 4's global step is the lazy greedy of Alg. 2
+    over the gathered local seeds, reported as the single bucket 0."""
     vtx_off, set_ids = inv
-    B = num_buckets(k, delta)
+    B = 1 if naive else num_buckets(k, delta)
     ls = np.zeros(P * k, dtype=np.int32)
     lg = np.zeros(P * k, dtype=np.int64)
     ln = np.zeros(P, dtype=np.int32)
@@ -275,7 +304,8 @@ def randgreedi(n: int, pool: Pool, inv, k: int, P: int, pseed: int, trunc: int,
     ns = np.zeros(1, dtype=np.int32)
     cov = np.zeros(1, dtype=np.int64)
     rc = _lib().orc_randgreedi(n, pool.theta, _p(pool.set_off), _p(pool.members), _p(vtx_off),
-                               _p(set_ids), k, P, pseed, trunc, delta, _p(ls), _p(lg), _p(ln),
+                               _p(set_ids), k, P, pseed, trunc, delta, int(naive), _p(ls),
+                               _p(lg), _p(ln),
                                _p(lc), _p(thr), _p(bc), _p(bn), _p(bs), _p(bg), _p(chosen),
                                _p(seeds), _p(gains), _p(ns), _p(cov))
     if rc:

@@ -99,13 +99,15 @@ KernelTimer::~KernelTimer() {
 
 namespace {
 std::mutex g_tune_mu;
-// IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER, IM_TUNE_INDEX_REPLICAS, IM_TUNE_RG_EVALS
-int64_t g_tune[4] = {1, 0, 4, 2};
+// IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER, IM_TUNE_INDEX_REPLICAS, IM_TUNE_RG_EVALS,
+// IM_TUNE_GREEDY_EVALS
+constexpr int kKnobs = 5;
+int64_t g_tune[kKnobs] = {1, 0, 4, 2, 0};
 }  // namespace
 
 int64_t tune_value(int32_t knob) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    return (knob >= 0 && knob < 4) ? g_tune[knob] : 0;
+    return (knob >= 0 && knob < kKnobs) ? g_tune[knob] : 0;
 }
 
 int num_sms() {
@@ -515,11 +517,12 @@ im_status im_max_k_cover(im_pool *p, int32_t k, const im_cover_opts *opts, int32
     if (opts) o = *opts;
     if (o.algo == IM_RANDGREEDI) {
         if (o.partitions < 1 || o.partitions > 4096 || o.alpha_num < 1 || o.alpha_den < 1 ||
-            o.alpha_num > o.alpha_den || !(o.delta > 0.0 && o.delta < 0.5)) {
+            o.alpha_num > o.alpha_den || !(o.delta > 0.0 && o.delta < 0.5) ||
+            (o.aggregator != IM_AGG_STREAM && o.aggregator != IM_AGG_GREEDY)) {
             set_error("im_max_k_cover: RandGreedi options out of range");
             return IM_ERR_INVALID_ARG;
         }
-    } else if (o.algo != IM_GREEDY_PLAIN) {
+    } else if (o.algo != IM_GREEDY_PLAIN && o.algo != IM_GREEDY_LAZY) {
         set_error("im_max_k_cover: unknown algorithm");
         return IM_ERR_INVALID_ARG;
     }
@@ -540,7 +543,8 @@ im_status im_max_k_cover(im_pool *p, int32_t k, const im_cover_opts *opts, int32
     IM_CUDA(cudaMemsetAsync(R + o_tail, 0, 64, st));
     im_status s = o.algo == IM_RANDGREEDI
                       ? randgreedi(p, k, &o, d_seeds, d_gains, d_nseeds, d_cov, st, d_status)
-                      : greedy_plain(p, k, d_seeds, d_gains, d_nseeds, d_cov, st, d_status);
+                      : greedy_select(p, k, o.algo == IM_GREEDY_LAZY, d_seeds, d_gains, d_nseeds,
+                                      d_cov, st, d_status);
     if (s != IM_OK) return s;
     int32_t hdr[6];
     IM_CUDA(cudaMemcpyAsync(hdr, R + o_tail, sizeof(hdr), cudaMemcpyDeviceToHost, st));
@@ -612,7 +616,10 @@ im_status im_tune_set(int32_t knob, int64_t value) {
                     (knob == IM_TUNE_INDEX_REPLICAS && (value == 1 || value == 2 || value == 4 ||
                                                         value == 8)) ||
                     (knob == IM_TUNE_RG_EVALS && (value == 1 || value == 2 || value == 4 ||
-                                                  value == 8));
+                                                  value == 8)) ||
+                    (knob == IM_TUNE_GREEDY_EVALS && (value == 0 || value == 1 || value == 2 ||
+                                                      value == 4 || value == 8 || value == 16 ||
+                                                      value == 32));
     if (ok) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[knob] = value;
@@ -623,7 +630,7 @@ im_status im_tune_set(int32_t knob, int64_t value) {
 }
 
 im_status im_tune_get(int32_t knob, int64_t *value) {
-    if (!value || knob < IM_TUNE_LT_GROUP || knob > IM_TUNE_RG_EVALS)
+    if (!value || knob < IM_TUNE_LT_GROUP || knob > IM_TUNE_GREEDY_EVALS)
         return IM_ERR_INVALID_ARG;
     *value = tune_value(knob);
     return IM_OK;

@@ -1153,7 +1153,11 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     const int32_t P = o->partitions;
     const int64_t n = p->g->n, theta = p->theta;
     const int64_t words = std::max<int64_t>(1, (theta + 31) / 32);
-    const int32_t B = num_buckets(k, o->delta);
+    // IM_AGG_GREEDY: Alg. 4's global step as written -- a greedy (the lazy one
+    // of Alg. 2) over the union of the gathered local seeds -- reported as a
+    // single "bucket" 0 without a threshold
+    const bool naive = o->aggregator == IM_AGG_GREEDY;
+    const int32_t B = naive ? 1 : num_buckets(k, o->delta);
     int64_t tr = ((int64_t)k * o->alpha_num + o->alpha_den - 1) / o->alpha_den;
     const int32_t trunc = (int32_t)std::max<int64_t>(1, std::min<int64_t>(k, tr));
 
@@ -1221,13 +1225,14 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     const size_t o_elems = take((size_t)trunc * P * 4);
     const size_t o_l = take(64);
     // bucket-mask stage (two-launch mode, automatic layout, B <= 64)
-    const bool use_masks = o->fused == 0 && tune_value(IM_TUNE_RG_CLUSTER) == 0 && B <= 64;
+    const bool use_masks = !naive && o->fused == 0 && tune_value(IM_TUNE_RG_CLUSTER) == 0 && B <= 64;
     const size_t o_mask = use_masks ? take((size_t)std::max<int64_t>(theta, 1) * 8) : 0;
     const size_t o_gbuf = use_masks ? take((size_t)2 * kMaskG * 64 * 4) : 0;
     const size_t o_bar = use_masks ? take(sizeof(GridBarrier)) : 0;
     const size_t o_sx = use_masks ? take((size_t)trunc * P * 4) : 0;
     const size_t o_sb = use_masks ? take((size_t)trunc * P * 8) : 0;
     const size_t o_sl = use_masks ? take((size_t)trunc * P * 8) : 0;
+    const size_t o_lazy = naive ? take(lazy_greedy_scratch(n, theta)) : 0;
     void *base = nullptr;
     s = pool_scratch(p, off, &base);
     if (s != IM_OK) return s;
@@ -1235,14 +1240,14 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     IM_CUDA(cudaMemsetAsync(Bs + o_flags, 0, (size_t)trunc * P * 4, st));
     // l = max_v |S(v)|: a lower bound on the optimum of the stream, u = k l
     int64_t l = 0;
-    {
+    if (!naive) {
         s = max_segment_length(p->vtx_off, n, (int64_t *)(Bs + o_l), st);
         if (s != IM_OK) return s;
         IM_CUDA(cudaMemcpyAsync(&l, Bs + o_l, 8, cudaMemcpyDeviceToHost, st));
         IM_CUDA(cudaStreamSynchronize(st));
     }
-    std::vector<int64_t> thr(B);
-    {
+    std::vector<int64_t> thr(B, 0);
+    if (!naive) {
         double guess = (double)l;
         for (int32_t b = 0; b < B; ++b) {
             thr[b] = (int64_t)std::ceil(guess / (2.0 * (double)k));
@@ -1295,7 +1300,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
                                                           prod_smem));
     if (per_sm < 1) return IM_ERR_UNSUPPORTED;
     const int resident = per_sm * num_sms();
-    bool fused = o->fused != 0 && resident >= 2;
+    bool fused = !naive && o->fused != 0 && resident >= 2;
     if (fused) {
         a.ncons = std::min<int32_t>(B, resident / 2);
         a.nprod = std::min<int32_t>(P, resident - a.ncons);
@@ -1316,7 +1321,19 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
         }
         IM_CUDA(cudaGetLastError());
         const int64_t want = tune_value(IM_TUNE_RG_CLUSTER);   // 0 auto, -1 off, 1..8
-        if (use_masks) {
+        if (naive) {
+            // the global greedy over the first `trunc` seeds of every part
+            int32_t W = (int32_t)tune_value(IM_TUNE_GREEDY_EVALS);
+            if (W <= 0) W = 16;
+            IM_CUDA(cudaMemsetAsync(p->rg_bucket_n, 0, sizeof(int32_t), st));
+            IM_CUDA(cudaMemsetAsync(p->rg_bucket_cov, 0, sizeof(int64_t), st));
+            IM_CUDA(cudaMemsetAsync(p->rg_stats + (size_t)P * 6, 0, 6 * 8, st));
+            s = greedy_lazy_launch(n, theta, p->vtx_off, p->set_ids, k, W, Bs + o_lazy,
+                                   p->rg_bucket_seeds, p->rg_bucket_gains, p->rg_bucket_n,
+                                   p->rg_bucket_cov, p->lz_stats, d_status, st,
+                                   p->rg_local_seeds, p->rg_local_n, P, trunc, k);
+            if (s != IM_OK) return s;
+        } else if (use_masks) {
             // buckets: one pass over each streamed subset serves all buckets
             int per = 0;
             IM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rg_stream_masks,
@@ -1338,7 +1355,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
             if (csmem <= kClusterSmemCap) break;
         }
         if (want < 0) CS = 16;   // global-memory bitmaps requested
-        if (use_masks) {
+        if (naive || use_masks) {
             // done above
         } else if (CS <= 8) {
             unsigned *counter = (unsigned *)(Bs + o_l) + 2;

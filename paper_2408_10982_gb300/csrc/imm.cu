@@ -90,7 +90,8 @@ im_status select_seeds(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d
     IM_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
     s = (o && o->algo == IM_RANDGREEDI)
             ? randgreedi(p, k, o, d_seeds, d_gains, d_ns, d_cov, st, d_status)
-            : greedy_plain(p, k, d_seeds, d_gains, d_ns, d_cov, st, d_status);
+            : greedy_select(p, k, o && o->algo == IM_GREEDY_LAZY, d_seeds, d_gains, d_ns, d_cov,
+                            st, d_status);
     if (s != IM_OK) return s;
     int64_t hc[3] = {0, 0, 0};
     IM_CUDA(cudaMemcpyAsync(&hc[0], d_cov, 8, cudaMemcpyDeviceToHost, st));

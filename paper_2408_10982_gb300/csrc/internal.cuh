@@ -150,24 +150,6 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// One cut point of the LT pick (see k_lt_guide), 32 bytes = one DRAM sector:
-// {running sum low word, high word, source u of the edge, u's first in-edge,
-//  u's in-degree, the edge's index within its in-list, 0, 0}.  Carrying u's
-// in-list lets the next step of a walk go straight to u's cut points.
-struct __align__(32) LtCut {
-    uint32_t cum_lo, cum_hi, src, src_eb;
-    uint32_t src_d, e, pad0, pad1;
-};
-
-__device__ __forceinline__ LtCut ld_lt_cut(const LtCut *p) {
-    LtCut c;
-    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(c.cum_lo), "=r"(c.cum_hi), "=r"(c.src), "=r"(c.src_eb), "=r"(c.src_d), "=r"(c.e),
-          "=r"(c.pad0), "=r"(c.pad1)
-        : "l"(p));
-    return c;
-}
-
 }  // namespace im
 
 // What a sampling kernel needs of one query: its graph and random stream.
@@ -179,7 +161,7 @@ struct QueryView {
     const uint4 *lt_vrec;
     const unsigned long long *lt_leaf;
     const unsigned long long *lt_tree;
-    const im::LtCut *lt_guide;
+    const uint4 *lt_guide;
     uint64_t seed;
     uint32_t n;
     uint32_t first;      // sample id of the query's first sample
@@ -199,7 +181,7 @@ struct im_graph {
     uint4 *lt_vrec;                  // [n] {edge offset, in-degree, tree offset, 0}
     unsigned long long *lt_leaf;     // [m]
     unsigned long long *lt_tree;     // [sum over vertices of the upper-level sizes]
-    im::LtCut *lt_guide;             // [m] inverse-CDF cut points (see k_lt_guide)
+    uint4 *lt_guide;                 // [m] inverse-CDF cut points (see k_lt_guide)
     // out-edge index, built on first im_spread: per source, the in-CSR ids
     // of its out-edges and their heads
     int64_t *out_off;                // [n+1]
@@ -244,6 +226,8 @@ struct im_pool {
     long long *rg_stats;              // [(P+B)*6] diagnostics
     size_t rg_cap_bytes;
     void *rg_block;
+    // last lazy greedy: rounds, candidate evaluations, entries scanned, list builds
+    long long lz_stats[4];
     // scratch arena (grown on demand) and per-call results
     void *scratch;
     size_t scratch_bytes;
@@ -404,6 +388,21 @@ im_status greedy_launch_view(int64_t n, int64_t theta, const int64_t *set_off,
                              int32_t *counts, uint32_t *covered, unsigned long long *block_best,
                              int max_grid, void *barrier, int32_t *seeds, int64_t *gains,
                              int32_t *nseeds, int64_t *coverage, int *status, cudaStream_t st);
+// The standard greedy's result on a pool: the lazy kernel (lazy = true, or
+// IM_TUNE_GREEDY_EVALS > 0) or the counts-decrement kernel (cover.cu).
+im_status greedy_select(im_pool *p, int32_t k, bool lazy, int32_t *d_seeds, int64_t *d_gains,
+                        int32_t *d_nseeds, int64_t *d_cov, cudaStream_t st, int *d_status);
+// lazy greedy (lazy.cu): scratch bytes, and the launch on caller scratch
+size_t lazy_greedy_scratch(int64_t n, int64_t theta);
+// With cand_seeds, the candidates are the first cand_take seeds of each of
+// cand_parts local solutions (RandGreedi's gathered seeds, Alg. 4).
+im_status greedy_lazy_launch(int64_t n, int64_t theta, const int64_t *vtx_off,
+                             const int32_t *set_ids, int32_t k, int32_t W, void *scratch,
+                             int32_t *seeds, int64_t *gains, int32_t *nseeds, int64_t *coverage,
+                             long long *stats_out, int *status, cudaStream_t st,
+                             const int32_t *cand_seeds = nullptr, const int32_t *cand_n = nullptr,
+                             int32_t cand_parts = 0, int32_t cand_take = 0,
+                             int32_t cand_stride = 0);
 im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_seeds,
                      int64_t *d_gains, int32_t *d_nseeds, int64_t *d_cov, cudaStream_t st,
                      int *d_status);

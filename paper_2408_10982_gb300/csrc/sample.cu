@@ -628,11 +628,10 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
     if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
 }
 
-// LT, one walk per thread.  A step is one Philox draw and one 32-byte cut
-// point (see k_lt_guide), which also carries the picked source's in-list, so
-// the walk needs one dependent load per step for any in-degree; a binary
-// search over the running sums (and the source's vertex record) runs only when
-// the draw lies past the cut point's edge.  The revisit test goes through a 1024-bit Bloom filter of
+// LT, one walk per thread.  A step is one Philox draw, the vertex record and
+// one guide entry (see k_lt_guide): two dependent loads for any in-degree,
+// with a binary search over the running sums only when the draw lies past
+// the guide's edge.  The revisit test goes through a 1024-bit Bloom filter of
 // the walk in shared memory (two hashes); only a hit is checked exactly, by
 // the whole warp scanning that walk's path.  Finished walks are copied to the
 // stage by the whole warp as well, after one warp-wide reservation.
@@ -668,10 +667,8 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
     bool active = false, exhausted = false;
     int64_t j = 0;
     uint32_t s = 0, cur = 0, k0 = 0, k1 = 0;
-    const uint4 *vrec = nullptr;
-    const LtCut *guide = nullptr;
+    const uint4 *vrec = nullptr, *guide = nullptr;
     const unsigned long long *leaf = nullptr;
-    uint32_t ceb = 0, cd = 0;                    // in-list of cur: first edge, in-degree
     int32_t len = 0;
     unsigned long long sexam = 0, exam = 0, abytes = 0;
     uint32_t sbytes = 0;
@@ -697,16 +694,13 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
                     k1 = seed_hi(V.seed);
                     s = V.first + (uint32_t)(j - __ldg(a.qstart + qi));
                     cur = rrr_root(V.seed, s, V.n);
-                    const uint4 vr = __ldg(vrec + cur);
-                    ceb = vr.x;
-                    cd = vr.y;
                     q[0] = (int32_t)cur;
 #pragma unroll
                     for (int w = 0; w < kBloomWords; ++w) bl[w * kLT1Threads] = 0u;
                     bloom_add(bl, cur);
                     len = 1;
                     sexam = 0;
-                    sbytes = 8u + 16u + 4u;   // set offset, root's vertex record, root write
+                    sbytes = 8u + 4u;                // set offset, root write
                     active = true;
                 } else {
                     exhausted = true;
@@ -717,35 +711,32 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
 
         // ---- one step of every active walk
         bool picked = false;
-        uint32_t u = 0, ueb = 0, ud = 0;
+        uint32_t u = 0;
         if (active) {
             const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
-            const uint32_t d = cd;
+            const uint4 vr = __ldg(vrec + cur);
+            const uint32_t d = vr.y;
             int64_t e = -1;
+            sbytes += 16u;                           // vertex record
             if (d > 0) {
-                const LtCut c = ld_lt_cut(guide + ceb + __umulhi(x, d));
-                const unsigned long long cum = ((unsigned long long)c.cum_hi << 32) | c.cum_lo;
-                sbytes += 32u;
+                const uint4 gv = __ldg(guide + vr.x + __umulhi(x, d));
+                const unsigned long long cum = ((unsigned long long)gv.y << 32) | gv.x;
+                sbytes += 16u;                       // cut point
                 if ((unsigned long long)x < cum) {
-                    e = c.e;
-                    u = c.src;
-                    ueb = c.src_eb;
-                    ud = c.src_d;
+                    e = gv.w;
+                    u = gv.z;
                 } else {
-                    uint32_t lo = c.e + 1, hi = d;   // first edge past the cut's with x < sum
+                    uint32_t lo = gv.w + 1, hi = d;  // first edge past the guide's with x < sum
                     while (lo < hi) {
                         const uint32_t mid = (lo + hi) >> 1;
-                        if ((unsigned long long)x < (__ldg(leaf + ceb + mid) >> 31)) hi = mid;
+                        if ((unsigned long long)x < (__ldg(leaf + vr.x + mid) >> 31)) hi = mid;
                         else lo = mid + 1;
-                        sbytes += 8u;
+                        sbytes += 8u;                // search probe
                     }
                     if (lo < d) {
                         e = lo;
-                        u = (uint32_t)(__ldg(leaf + ceb + lo) & 0x7fffffffull);
-                        const uint4 vr = __ldg(vrec + u);
-                        ueb = vr.x;
-                        ud = vr.y;
-                        sbytes += 8u + 16u;
+                        u = (uint32_t)(__ldg(leaf + vr.x + lo) & 0x7fffffffull);
+                        sbytes += 8u;                // picked leaf
                     }
                 }
             }
@@ -777,8 +768,6 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
                 ++len;
                 sbytes += 4u;                        // member write
                 cur = u;
-                ceb = ueb;
-                cd = ud;
             } else {
                 ovf = true;
             }
@@ -984,12 +973,11 @@ __global__ void __launch_bounds__(256) k_lt_index_block(
 // vertex v (in-edges [eb, eb + d)) falls in bucket b = floor(x d / 2^32); the
 // smallest draw of bucket b is lo_b = ceil(b 2^32 / d).  guide[eb + b]
 // describes the first in-edge e whose running sum exceeds lo_b, or the last
-// in-edge when none does: its running sum, its source u, u's own in-list
-// (first edge, in-degree) and e.  Every edge before e has a running sum
-// <= lo_b <= x, so x picks e exactly when x < running sum(e); otherwise the
-// pick lies after e (or there is none).
+// in-edge when none does: {running sum low word, high word, source, e}.
+// Every edge before e has a running sum <= lo_b <= x, so x picks e exactly
+// when x < running sum(e); otherwise the pick lies after e (or there is none).
 __global__ void k_lt_guide(const int64_t *in_off, const unsigned long long *leaf, int64_t n,
-                           int64_t m, LtCut *guide) {
+                           int64_t m, uint4 *guide) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
          t += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = n - 1;                  // vertex owning position t
@@ -1010,17 +998,8 @@ __global__ void k_lt_guide(const int64_t *in_off, const unsigned long long *leaf
         const int64_t e = l2 < d ? l2 : d - 1;
         const unsigned long long r = leaf[eb + e];
         const unsigned long long cum = r >> 31;
-        const uint32_t u = (uint32_t)(r & 0x7fffffffull);
-        const int64_t ub = in_off[u];
-        LtCut c;
-        c.cum_lo = (uint32_t)cum;
-        c.cum_hi = (uint32_t)(cum >> 32);
-        c.src = u;
-        c.src_eb = (uint32_t)ub;
-        c.src_d = (uint32_t)(in_off[u + 1] - ub);
-        c.e = (uint32_t)e;
-        c.pad0 = c.pad1 = 0u;
-        guide[t] = c;
+        guide[t] = make_uint4((uint32_t)cum, (uint32_t)(cum >> 32), (uint32_t)(r & 0x7fffffffull),
+                              (uint32_t)e);
     }
 }
 
@@ -1312,8 +1291,7 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
     // the index itself: handed to g once complete, freed on any failure
     struct Index {
         unsigned long long *leaf = nullptr, *tree = nullptr;
-        uint4 *vrec = nullptr;
-        LtCut *guide = nullptr;
+        uint4 *vrec = nullptr, *guide = nullptr;
         ~Index() {
             if (leaf || tree || vrec || guide) {
                 cudaDeviceSynchronize();
@@ -1358,7 +1336,7 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
                 t.flags);
     }
     IM_CUDA(cudaGetLastError());
-    IM_CUDA(cudaMalloc(&x.guide, (size_t)std::max<int64_t>(m, 1) * sizeof(LtCut)));
+    IM_CUDA(cudaMalloc(&x.guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
     if (m > 0) {
         KernelTimer kt(st, "lt_index");
         k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, x.leaf, n, m, x.guide);
@@ -1373,8 +1351,7 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
     g->lt_guide = x.guide;
     g->lt_leaf = x.leaf;
     x.leaf = x.tree = nullptr;
-    x.vrec = nullptr;
-    x.guide = nullptr;
+    x.vrec = x.guide = nullptr;
     return IM_OK;
 }
 

@@ -27,7 +27,8 @@ IM_ERR_BUSY = -6
 IM_ERR_UNSUPPORTED = -7
 
 IM_IC, IM_LT = 0, 1
-IM_GREEDY_PLAIN, IM_RANDGREEDI = 0, 1
+IM_GREEDY_PLAIN, IM_RANDGREEDI, IM_GREEDY_LAZY = 0, 1, 2
+IM_AGG_STREAM, IM_AGG_GREEDY = 0, 1
 
 
 class ImError(RuntimeError):
@@ -41,12 +42,14 @@ class CoverOpts(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("partitions", ctypes.c_int32),
                 ("alpha_num", ctypes.c_int32), ("alpha_den", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("partition_seed", ctypes.c_uint64),
-                ("fused", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fused", ctypes.c_int32), ("aggregator", ctypes.c_int32)]
 
 
 def cover_opts(algo: int = IM_GREEDY_PLAIN, partitions: int = 148, alpha: tuple = (1, 1),
-               delta: float = 0.077, partition_seed: int = 42, fused: bool = True) -> CoverOpts:
-    return CoverOpts(algo, partitions, alpha[0], alpha[1], delta, partition_seed, int(fused), 0)
+               delta: float = 0.077, partition_seed: int = 42, fused: bool = True,
+               aggregator: int = IM_AGG_STREAM) -> CoverOpts:
+    return CoverOpts(algo, partitions, alpha[0], alpha[1], delta, partition_seed, int(fused),
+                     aggregator)
 
 
 _LIB = None
@@ -84,6 +87,7 @@ def lib():
             "im_partition": ([i64, i32, u64, vp, vp], ctypes.c_int),
             "im_pool_sample_bytes": ([vp, vp], ctypes.c_int),
             "im_randgreedi_stats": ([vp, vp, vp], ctypes.c_int),
+            "im_greedy_stats": ([vp, vp], ctypes.c_int),
             "im_max_k_cover_noalloc": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp, vp],
                                        ctypes.c_int),
             "im_pool_reserve": ([vp, i64, i64], ctypes.c_int),
@@ -427,6 +431,14 @@ def im_randgreedi_stats(p, P: int, B: int, stream=None) -> np.ndarray:
     return out.reshape(P + B, 6)
 
 
+def im_greedy_stats(p) -> dict:
+    """The pool's last lazy-greedy cover: rounds, candidate evaluations,
+    covering-subset entries they scanned, builds of the sorted bound list."""
+    out = np.zeros(4, np.int64)
+    _check(lib().im_greedy_stats(p, out.ctypes.data), "im_greedy_stats")
+    return dict(rounds=int(out[0]), evals=int(out[1]), scanned=int(out[2]), builds=int(out[3]))
+
+
 def im_pool_sample_bytes(p) -> int:
     b = ctypes.c_int64()
     _check(lib().im_pool_sample_bytes(p, ctypes.byref(b)), "im_pool_sample_bytes")
@@ -437,6 +449,7 @@ IM_TUNE_LT_GROUP = 0
 IM_TUNE_RG_CLUSTER = 1
 IM_TUNE_INDEX_REPLICAS = 2
 IM_TUNE_RG_EVALS = 3
+IM_TUNE_GREEDY_EVALS = 4
 
 
 def im_tune_set(knob: int, value: int):

@@ -52,16 +52,18 @@ def _no_gpu():
 
 
 def test_tuning_knobs_defaults_values_and_rejections(libpath):
-    """The knob values include/im.h documents: defaults 1, 0, 4, 2; every
+    """The knob values include/im.h documents: defaults 1, 0, 4, 2, 0; every
     allowed value is stored; anything else is IM_ERR_INVALID_ARG and leaves
     the knob unchanged."""
     from paper_2408_10982_gb300 import im
     allowed = {im.IM_TUNE_LT_GROUP: [1, 8, 16, 32],
                im.IM_TUNE_RG_CLUSTER: [-1, 0, 1, 2, 4, 8],
                im.IM_TUNE_INDEX_REPLICAS: [1, 2, 4, 8],
-               im.IM_TUNE_RG_EVALS: [1, 2, 4, 8]}
+               im.IM_TUNE_RG_EVALS: [1, 2, 4, 8],
+               im.IM_TUNE_GREEDY_EVALS: [0, 1, 2, 4, 8, 16, 32]}
     defaults = {im.IM_TUNE_LT_GROUP: 1, im.IM_TUNE_RG_CLUSTER: 0,
-                im.IM_TUNE_INDEX_REPLICAS: 4, im.IM_TUNE_RG_EVALS: 2}
+                im.IM_TUNE_INDEX_REPLICAS: 4, im.IM_TUNE_RG_EVALS: 2,
+                im.IM_TUNE_GREEDY_EVALS: 0}
     before = {k: im.im_tune_get(k) for k in allowed}
     try:
         for k in allowed:
@@ -78,7 +80,7 @@ def test_tuning_knobs_defaults_values_and_rejections(libpath):
                     im.im_tune_set(k, bad)
                 assert e.value.status == im.IM_ERR_INVALID_ARG
                 assert im.im_tune_get(k) == keep
-        for bad_knob in (-1, 4, 99):
+        for bad_knob in (-1, 5, 99):
             with pytest.raises(im.ImError):
                 im.im_tune_set(bad_knob, 1)
             with pytest.raises(im.ImError):

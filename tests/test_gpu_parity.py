@@ -195,15 +195,17 @@ def test_empty_pool_cover(im):
     assert len(c.seeds) == 0 and c.coverage == 0
 
 
-def _rg_compare(im, g, model, theta, k, Pn, alpha, delta, fused, seed=42, pseed=42):
+def _rg_compare(im, g, model, theta, k, Pn, alpha, delta, fused, seed=42, pseed=42,
+                naive=False):
     G, P = gpu_pool(im, g, model, seed, [(0, theta)])
     ref = O.sample(model, g, seed, 0, theta)
     inv = O.invert(g.n, ref)
     trunc = O.trunc_count(k, *alpha)
-    r = O.randgreedi(g.n, ref, inv, k, Pn, pseed, trunc, delta)
-    opts = im.cover_opts(im.IM_RANDGREEDI, Pn, alpha, delta, pseed, fused)
+    r = O.randgreedi(g.n, ref, inv, k, Pn, pseed, trunc, delta, naive=naive)
+    opts = im.cover_opts(im.IM_RANDGREEDI, Pn, alpha, delta, pseed, fused,
+                         im.IM_AGG_GREEDY if naive else im.IM_AGG_STREAM)
     c = P.cover(k, opts)
-    B = O.num_buckets(k, delta)
+    B = 1 if naive else O.num_buckets(k, delta)
     d = P.randgreedi_details(k, Pn, B)
     assert np.array_equal(d["local_n"], r.local_n)
     for p in range(Pn):

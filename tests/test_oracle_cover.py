@@ -190,3 +190,80 @@ def test_trunc_count():
     assert trunc_count(100, 1, 8) == 13       # ceil(12.5)
     assert trunc_count(5, 1, 100) == 1
     assert trunc_count(7, 1, 1) == 7
+
+
+# ---------------------------------------------------------------------------
+# Lazy greedy (Alg. 2) and Alg. 4's non-streaming global step
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("gseed", range(8))
+@pytest.mark.parametrize("k", [1, 3, 6, 40])
+def test_lazy_greedy_equals_from_scratch_definition(orc, gseed, k):
+    """Stale gains are upper bounds (submodularity), so Alg. 2 with the key
+    order (gain, smaller id) picks what the standard greedy picks; also with a
+    candidate list, and past the point where every gain is zero."""
+    g, pool, inv, S = _instance(orc, gseed=gseed + 70, model=gseed % 2)
+    c = orc.lazy_greedy(g.n, pool, inv, k)
+    seeds, gains, cov = brute.greedy_definition(S, k)
+    assert c.seeds.tolist() == seeds and c.gains.tolist() == gains and c.coverage == cov
+    cand = [v for v in range(g.n) if (v * 5 + gseed) % 3 != 0]
+    c2 = orc.lazy_greedy(g.n, pool, inv, k, np.array(cand, dtype=np.int32))
+    s2, g2, cov2 = brute.greedy_definition(S, k, cand)
+    assert c2.seeds.tolist() == s2 and c2.gains.tolist() == g2 and c2.coverage == cov2
+
+
+@pytest.mark.parametrize("theta", [3, 40, 5000])
+def test_lazy_greedy_equals_standard_greedy_on_rmat(orc, theta):
+    """Tie-heavy (theta = 3: almost every gain is 1) to many sets."""
+    g = inputs.rmat_graph(1 << 12, 1 << 16, 3, "lt")
+    pool = orc.sample(orc.LT, g, 9, 0, theta)
+    inv = orc.invert(g.n, pool)
+    for k in (1, 10, 100):
+        a, b = orc.greedy(g.n, pool, inv, k), orc.lazy_greedy(g.n, pool, inv, k)
+        assert a.seeds.tolist() == b.seeds.tolist() and a.gains.tolist() == b.gains.tolist()
+        assert a.coverage == b.coverage
+
+
+def test_lazy_greedy_hand_worked():
+    """Alg. 2 step by step on R0 = {0, 1}, R1 = {1, 2}, R2 = {2}, R3 = {0, 3}:
+    S(0) = {0, 3}, S(1) = {0, 1}, S(2) = {1, 2}, S(3) = {3}.  Heap keys 2, 2, 2, 1.
+    Pop 0 (ties: smallest id), gain 2 >= top key 2 (vertex 1, larger id): take 0.
+    Pop 1, gain |{0,1} - {0,3}| = 1 < top key 2 (vertex 2): push (1, 1).
+    Pop 2, gain 2 >= top 1: take 2.  Pop 1, gain 0 < top key 1 (vertex 3):
+    push (1, 0).  Pop 3, gain 0; the top (vertex 1, key 0) ranks above it: push
+    (3, 0).  Pop 1, gain 0, ranks above the top (3, 0): it would be taken with
+    gain 0, so the selection stops.  Seeds [0, 2], gains [2, 2]."""
+    import oracle
+    oracle.build()
+
+    class P:
+        set_off = np.array([0, 2, 4, 5, 7], dtype=np.int64)
+        members = np.array([0, 1, 1, 2, 2, 0, 3], dtype=np.int32)
+        theta = 4
+    inv = oracle.invert(4, P)
+    c = oracle.lazy_greedy(4, P, inv, 4)
+    assert c.seeds.tolist() == [0, 2] and c.gains.tolist() == [2, 2] and c.coverage == 4
+
+
+@pytest.mark.parametrize("gseed", range(5))
+@pytest.mark.parametrize("P,trunc", [(3, 1), (4, 2), (2, 3)])
+def test_randgreedi_naive_global_step(orc, gseed, P, trunc):
+    """Alg. 4 as written: the global solution is the greedy over the union of
+    the gathered local seeds (the first `trunc` of every part); the answer is
+    the better of it and the best local solution (ties: the global one)."""
+    g, pool, inv, S = _instance(orc, n=16, m=70, theta=60, gseed=gseed + 90, model=gseed % 2)
+    k, pseed = 3, 23 + gseed
+    rg = orc.randgreedi(g.n, pool, inv, k, P, pseed, trunc, 0.1, naive=True)
+    ref = orc.randgreedi(g.n, pool, inv, k, P, pseed, trunc, 0.1)
+    assert np.array_equal(rg.local_seeds, ref.local_seeds)
+    assert np.array_equal(rg.local_cov, ref.local_cov)
+    gathered = sorted(int(rg.local_seeds[p, j]) for p in range(P)
+                      for j in range(min(trunc, int(rg.local_n[p]))))
+    seeds, gains, cov = brute.greedy_definition(S, k, gathered)
+    assert rg.buckets.n.tolist() == [len(seeds)] and rg.thr.tolist() == [0]
+    assert rg.buckets.seeds[0, : len(seeds)].tolist() == seeds
+    assert rg.buckets.gains[0, : len(seeds)].tolist() == gains
+    assert int(rg.buckets.cov[0]) == cov
+    assert rg.coverage == max(cov, int(rg.local_cov.max()))
+    assert rg.coverage == brute.coverage(S, rg.seeds.tolist())
+    assert (rg.chosen == -1) == (cov >= int(rg.local_cov.max()))
