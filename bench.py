@@ -392,6 +392,9 @@ def run_ours(args):
         lj = inputs.graph_livejournal_like_both(SEED)
         line["ic"] = bench_ic(im, torch, lj["trivalency"])
         line["imm"] = bench_imm(im, torch, lj["wc"])
+        del lj
+        line["paper_weights"] = bench_paper_weights(im, torch)
+        line["opim"] = bench_opim(im, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -743,6 +746,100 @@ def bench_imm(im, torch, g):
             "final_entries": int(info.final_entries), "coverage": int(cov),
             "num_seeds": int(len(seeds)), "final_examined_edges": int(info.examined),
             "phase_ms": {k: round(v[1], 3) for k, v in sorted(prof.items())}}
+
+
+def bench_opim(im, torch):
+    """OPIM with GreediRIS-trunc seed selection, the setting of the paper's
+    Table 6 (k = 1000, eps = 0.01, halves capped at 2^20 sets, bucket spacing
+    0.0562 for 63 buckets, delta = 1/n) on the rmat20-lt graph: per truncation
+    alpha, the seed-selection time over all rounds, the rounds' sampling and
+    scoring time, and the instance-wise guarantee; the plain greedy beside it."""
+    g = inputs.graph_lt_scale20(SEED)
+    G = im.Graph(g)
+    k, eps, cap = 1000, 0.01, 1 << 20
+    out = {"workload": "rmat20-lt, OPIM: k=1000, eps=0.01, delta=1/n, R1/R2 capped at 2^20 "
+                       "sets each; GreediRIS-trunc 148 parts, bucket delta 0.0562 (B=63)"}
+    im.im_opim(G.handle, im.IM_LT, 10, 0.5, 0.01, SEED, 1 << 14)     # warm-up
+    runs = [("plain_greedy", None)] + [
+        (f"alpha_{a[0]}/{a[1]}", im.cover_opts(im.IM_RANDGREEDI, PARTS, a, 0.0562, SEED,
+                                               fused=False))
+        for a in ((1, 1), (1, 2), (1, 4), (1, 8))]
+    for name, opts in runs:
+        im.im_profile_reset()
+        im.im_profile_enable(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seeds, info = im.im_opim(G.handle, im.IM_LT, k, eps, 1.0 / g.n, SEED, cap, opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        im.im_profile_enable(False)
+        prof = im.im_profile_read()
+        sel = sum(v[1] for kk, v in prof.items() if kk.startswith(("randgreedi", "greedy",
+                                                                     "partition", "max_subset")))
+        samp = sum(v[1] for kk, v in prof.items() if kk.startswith(("sample", "sort_sets", "scan")))
+        idx = sum(v[1] for kk, v in prof.items() if kk.startswith("index"))
+        score = sum(v[1] for kk, v in prof.items() if kk.startswith("opim"))
+        r = info.rounds
+        out[name] = {"ms": round(1000 * dt, 1), "seed_select_ms": round(sel, 2),
+                     "index_ms": round(idx, 2), "sampling_ms": round(samp, 2),
+                     "scoring_ms": round(score, 2), "rounds": r,
+                     "theta_per_half": int(info.theta[r - 1]),
+                     "guarantee": round(info.guarantee, 4),
+                     "guarantee_per_round": [round(x, 4) for x in info.alpha[:r]],
+                     "num_seeds": int(len(seeds))}
+    G.close()
+    return out
+
+
+def bench_paper_weights(im, torch):
+    """The paper's own weight model (Sec. 4.1, U[0, 0.1] per edge) on R-MAT
+    scale 20: IC with 16,384 sets (15% of them hold a ~10^5-vertex giant
+    component) and LT (the same draws scaled per vertex to sum to at most 1)
+    with 1,048,576 sets; sampling, plain greedy and RandGreedi (148 parts,
+    alpha 1/4) at k = 100.  The first 16 IC sets are checked against the
+    oracle."""
+    import oracle as O
+    opts_rg = im.cover_opts(im.IM_RANDGREEDI, PARTS, ALPHA, DELTA, SEED, fused=False)
+    out = {}
+    for model, wts, theta in ((im.IM_IC, "u0.1", 16384), (im.IM_LT, "lt-u0.1", 1 << 20)):
+        g = inputs.rmat_graph(1 << 20, 1 << 24, SEED, wts)
+        G = im.Graph(g)
+        cap = theta * (40000 if model == im.IM_IC else 64)
+        p = im.Pool(G, theta, cap)
+        p.sample(model, SEED, 0, min(theta, 1024))       # warm-up (builds the LT index)
+        p.reset()
+        im.im_profile_reset()
+        im.im_profile_enable(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p.sample(model, SEED, 0, theta)
+        torch.cuda.synchronize()
+        t_s = time.perf_counter() - t0
+        c = p.cover(K)
+        torch.cuda.synchronize()
+        t_g = time.perf_counter() - t0 - t_s
+        r = p.cover(K, opts_rg)
+        torch.cuda.synchronize()
+        t_r = time.perf_counter() - t0 - t_s - t_g
+        im.im_profile_enable(False)
+        prof = im.im_profile_read()
+        _, total, examined = p.info()
+        e = {"theta": theta, "entries": total, "examined_edges": examined,
+             "sample_ms": round(1000 * t_s, 2), "edges_per_s": examined / t_s,
+             "greedy_ms": round(1000 * t_g, 2), "randgreedi_ms": round(1000 * t_r, 2),
+             "coverage_greedy": int(c.coverage), "coverage_randgreedi": int(r.coverage),
+             "phase_ms": {k2: round(v[1], 3) for k2, v in sorted(prof.items())}}
+        if model == im.IM_IC:
+            set_off, members = p.export()
+            ref = O.sample(O.IC, g, SEED, 0, 16)
+            e["bit_exact_first_16"] = bool(np.array_equal(set_off[:17], ref.set_off) and
+                                           np.array_equal(members[:ref.set_off[-1]], ref.members))
+        out["ic" if model == im.IM_IC else "lt"] = e
+        p.close()
+        G.close()
+    out["workload"] = ("R-MAT scale 20 (1,048,576 vertices, 16,777,216 edges), edge probabilities "
+                       "U[0, 0.1] (IC; LT scaled per vertex to sum <= 1), k=100")
+    return out
 
 
 def bench_ic(im, torch, g):

@@ -378,6 +378,50 @@ im_status im_solve(const im_graph *g, im_model model, int32_t k, double eps, dou
                    uint64_t seed, const im_cover_opts *opts, int32_t *seeds, int32_t *num_seeds,
                    int64_t *coverage, int64_t *theta, im_solve_info *info, void *stream);
 
+/* ---- OPIM with GreediRIS seed selection (Sec. 3.3.2 and Sec. 4.4, Table 6) --
+ * OPIM (Tang et al. 2018; the paper runs its RandGreedi inside it) splits each
+ * round's samples into a selection half R1 (sample ids 0, 1, ...) and a
+ * validation half R2 (ids 2^31, 2^31 + 1, ...).  Round i = 1 .. i_max: both
+ * halves grow to theta_i = theta_0 2^(i-1) sets (appending ids); seeds are
+ * selected on R1 as opts says (NULL: plain greedy; RandGreedi with its
+ * truncation alpha: GreediRIS-trunc); cov1 = their coverage of R1, cov2 =
+ * the sets of R2 that hold a seed, cov1u = cov1 + the k largest marginal
+ * gains left on R1 (an upper bound on the optimal k-set's coverage of R1,
+ * valid for any seed set); then, with a = ln(3 i_max / delta),
+ *   sigma_l = ((sqrt(cov2 + 2a/9) - sqrt(a/2))^2 - a/18) n / theta_i,
+ *   sigma_u = (sqrt(cov1u + a/2) + sqrt(a/2))^2 n / theta_i,
+ * and the round's instance-wise guarantee is sigma_l / sigma_u; the rounds
+ * stop once it reaches 1 - 1/e - eps, or after the last round.
+ *   theta_max = 2n ((1-1/e) sqrt(ln(6/delta)) + sqrt((1-1/e)(ln C(n,k)
+ *               + ln(6/delta))))^2 / (eps^2 k),
+ *   theta_0 = ceil(theta_max eps^2 k / n), i_max = max(1, ceil(log2(
+ *   theta_max / theta_0))), or, with theta_cap > 0, the last round whose
+ *   theta_i <= theta_cap (the paper stops near 2^20 sets).  Natural logs.
+ * Outputs: seeds int32[k] (host or device) and num_seeds of the last round;
+ * info (optional) records every round.  IM_ERR_CAPACITY when a half would
+ * need 2^31 or more sets (pass a cap).  Synchronises the stream. */
+typedef struct {
+    int32_t rounds;               /* rounds run */
+    int32_t keep_pools;           /* in: hand R1 / R2 to the caller */
+    int64_t theta[64];            /* sets in each half, per round */
+    int64_t cov1[64];             /* coverage of the round's seeds on R1 */
+    int64_t cov2[64];             /* sets of R2 that hold a seed */
+    int64_t cov1_upper[64];       /* cov1 + the k largest marginal gains on R1 */
+    double alpha[64];             /* sigma_l / sigma_u of each round */
+    double sigma_lower, sigma_upper, guarantee;   /* of the returned seeds */
+    double theta_max;
+    int64_t theta0;
+    int32_t max_rounds;           /* i_max */
+    int32_t reserved;
+    double a;                     /* ln(3 i_max / delta) */
+    im_pool *r1_pool;             /* out (keep_pools): the caller destroys them */
+    im_pool *r2_pool;
+} im_opim_info;
+
+im_status im_opim(const im_graph *g, im_model model, int32_t k, double eps, double delta,
+                  uint64_t seed, int64_t theta_cap, const im_cover_opts *opts, int32_t *seeds,
+                  int32_t *num_seeds, im_opim_info *info, void *stream);
+
 /* ---- many queries at once (batching; not in the paper) -----------------------
  * A query: a resident graph, a model, k, theta (sample ids 0 .. theta-1) and
  * its Philox seed.  im_solve_batch solves nq queries in a fixed number of

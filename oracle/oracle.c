@@ -619,3 +619,53 @@ int orc_imm_check(int64_t n, int64_t coverage, int64_t theta_i, int32_t i, doubl
 
 /* Final sample count theta = ceil(lambda* / LB). */
 int64_t orc_imm_final_theta(double lamstar, double lb) { return (int64_t)ceil(lamstar / lb); }
+
+/* ------------------------------------------------------------------------ */
+/* OPIM's instance-wise guarantee (Sec. 3.3.2 / Sec. 4.4 use OPIM of Tang   */
+/* et al. 2018 in place of IMM; the paper prints none of its formulas, so   */
+/* they are written out here from that work, natural logs throughout):      */
+/*   theta_max = 2n ((1-1/e) sqrt(ln(6/delta))                              */
+/*               + sqrt((1-1/e)(ln C(n,k) + ln(6/delta))))^2 / (eps^2 k)    */
+/*   theta_0 = ceil(theta_max eps^2 k / n), theta_i = theta_0 2^(i-1)       */
+/*   i_max = max(1, ceil(log2(theta_max / theta_0))), lowered to the last   */
+/*   round whose theta_i stays within cap (cap > 0)                         */
+/*   a = ln(3 i_max / delta)  (the failure budget of one bound in a round)  */
+/* out: [0] theta_max, [1] theta_0, [2] i_max, [3] a.                       */
+/* ------------------------------------------------------------------------ */
+void orc_opim_constants(int64_t n, int32_t k, double eps, double delta, int64_t cap,
+                        double out[4]) {
+    const double dn = (double)n;
+    const double lncnk = lgamma(dn + 1.0) - lgamma((double)k + 1.0) - lgamma(dn - (double)k + 1.0);
+    const double one_e = 1.0 - exp(-1.0);
+    const double l6 = log(6.0 / delta);
+    const double s = one_e * sqrt(l6) + sqrt(one_e * (lncnk + l6));
+    const double tmax = 2.0 * dn * s * s / (eps * eps * (double)k);
+    const double t0 = ceil(tmax * eps * eps * (double)k / dn);
+    int32_t imax = (int32_t)ceil(log2(tmax / t0));
+    if (imax < 1) imax = 1;
+    if (cap > 0) {
+        int32_t fit = 1;
+        while (fit < imax && ldexp(t0, fit) <= (double)cap) ++fit;   /* theta_{fit+1} <= cap */
+        imax = fit;
+    }
+    out[0] = tmax;
+    out[1] = t0;
+    out[2] = (double)imax;
+    out[3] = log(3.0 * (double)imax / delta);
+}
+
+/* Lower confidence bound on the spread of S from its coverage cov2 of the */
+/* theta validation sets R2: the x solving cov2 = x + a/3 + sqrt(a^2/9 + 2ax) */
+/* (upper martingale tail at budget e^-a), times n / theta.                 */
+double orc_opim_lower(int64_t cov2, int64_t theta, int64_t n, double a) {
+    const double r = sqrt((double)cov2 + 2.0 * a / 9.0) - sqrt(a / 2.0);
+    return (r * r - a / 18.0) * (double)n / (double)theta;
+}
+
+/* Upper confidence bound on OPT from an upper bound cov1u of the optimal  */
+/* k-set's coverage of the theta selection sets R1: the x solving           */
+/* cov1u = x - sqrt(2ax) (lower tail), times n / theta.                     */
+double orc_opim_upper(int64_t cov1u, int64_t theta, int64_t n, double a) {
+    const double r = sqrt((double)cov1u + a / 2.0) + sqrt(a / 2.0);
+    return r * r * (double)n / (double)theta;
+}

@@ -11,7 +11,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libim.so")
 HEADERS = [os.path.join(CSRC, "internal.cuh"),
            os.path.join(os.path.dirname(HERE), "include", "im.h")]
-SOURCES = ["scan.cu", "sample.cu", "index.cu", "cover.cu", "lazy.cu", "api.cu", "noalloc.cu", "imm.cu", "batch.cu", "server.cu", "spread.cu", "tune.cu"]
+SOURCES = ["scan.cu", "sample.cu", "index.cu", "cover.cu", "lazy.cu", "api.cu", "noalloc.cu", "imm.cu", "opim.cu", "batch.cu", "server.cu", "spread.cu", "tune.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -53,8 +53,6 @@ im_status pool_grow(im_pool *p, int64_t max_sets, int64_t max_entries, cudaStrea
     return IM_OK;
 }
 
-namespace {
-
 // Appends ids [first, first + count) to the pool, growing it when needed.
 im_status sample_growing(const im_graph *g, im_model model, uint64_t seed, uint64_t first,
                          uint64_t count, im_pool *p, cudaStream_t st) {
@@ -102,7 +100,6 @@ im_status select_seeds(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d
     return IM_OK;
 }
 
-}  // namespace
 }  // namespace im
 
 using namespace im;

@@ -392,6 +392,14 @@ im_status greedy_launch_view(int64_t n, int64_t theta, const int64_t *set_off,
 // IM_TUNE_GREEDY_EVALS > 0) or the counts-decrement kernel (cover.cu).
 im_status greedy_select(im_pool *p, int32_t k, bool lazy, int32_t *d_seeds, int64_t *d_gains,
                         int32_t *d_nseeds, int64_t *d_cov, cudaStream_t st, int *d_status);
+// imm.cu: append ids [first, first + count) to a pool, growing it; and one
+// SelectSeeds (index build + the cover opts asks for) with its coverage
+// read back to the host.
+im_status sample_growing(const im_graph *g, im_model model, uint64_t seed, uint64_t first,
+                         uint64_t count, im_pool *p, cudaStream_t st);
+im_status select_seeds(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_seeds,
+                       int64_t *d_gains, int32_t *d_ns, int64_t *d_cov, int *d_status,
+                       int64_t *coverage, cudaStream_t st);
 // lazy greedy (lazy.cu): scratch bytes, and the launch on caller scratch
 size_t lazy_greedy_scratch(int64_t n, int64_t theta);
 // With cand_seeds, the candidates are the first cand_take seeds of each of

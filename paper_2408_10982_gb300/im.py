@@ -104,6 +104,8 @@ def lib():
             "im_solve_batch": ([vp, vp, i32, i32, vp, vp, vp, vp], ctypes.c_int),
             "im_solve": ([vp, ctypes.c_int, i32, ctypes.c_double, ctypes.c_double, u64, vp, vp,
                           vp, vp, vp, vp, vp], ctypes.c_int),
+            "im_opim": ([vp, ctypes.c_int, i32, ctypes.c_double, ctypes.c_double, u64, i64, vp,
+                         vp, vp, vp, vp], ctypes.c_int),
             "im_tune_set": ([i32, i64], ctypes.c_int),
             "im_tune_get": ([i32, vp], ctypes.c_int),
             "im_profile_enable": ([i32], ctypes.c_int),
@@ -271,6 +273,33 @@ class SolveInfo(ctypes.Structure):
                 ("round_entries", ctypes.c_int64), ("final_entries", ctypes.c_int64),
                 ("examined", ctypes.c_int64), ("round_pool", ctypes.c_void_p),
                 ("final_pool", ctypes.c_void_p)]
+
+
+class OpimInfo(ctypes.Structure):
+    """im_opim_info (see include/im.h)."""
+    _fields_ = [("rounds", ctypes.c_int32), ("keep_pools", ctypes.c_int32),
+                ("theta", ctypes.c_int64 * 64), ("cov1", ctypes.c_int64 * 64),
+                ("cov2", ctypes.c_int64 * 64), ("cov1_upper", ctypes.c_int64 * 64),
+                ("alpha", ctypes.c_double * 64), ("sigma_lower", ctypes.c_double),
+                ("sigma_upper", ctypes.c_double), ("guarantee", ctypes.c_double),
+                ("theta_max", ctypes.c_double), ("theta0", ctypes.c_int64),
+                ("max_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("a", ctypes.c_double), ("r1_pool", ctypes.c_void_p),
+                ("r2_pool", ctypes.c_void_p)]
+
+
+def im_opim(g, model: int, k: int, eps: float, delta: float, seed: int, theta_cap: int = 0,
+            opts: CoverOpts | None = None, stream=None, keep_pools: bool = False):
+    """OPIM rounds with GreediRIS seed selection: returns (seeds, info).  With
+    keep_pools, info.r1_pool / info.r2_pool must be destroyed by the caller."""
+    seeds = np.zeros(k, np.int32)
+    ns = ctypes.c_int32()
+    info = OpimInfo()
+    info.keep_pools = 1 if keep_pools else 0
+    _check(lib().im_opim(g, model, k, eps, delta, seed, theta_cap,
+                         None if opts is None else ctypes.byref(opts), seeds.ctypes.data,
+                         ctypes.byref(ns), ctypes.byref(info), _stream(stream)), "im_opim")
+    return seeds[: ns.value].copy(), info
 
 
 class Query(ctypes.Structure):

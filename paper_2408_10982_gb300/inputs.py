@@ -150,11 +150,28 @@ def weights_inverse_indegree(in_off: np.ndarray) -> np.ndarray:
     return np.repeat(per_v.astype(np.uint32), d)
 
 
-def weights_uniform_random(m: int, seed: int, hi: float = 0.1) -> np.ndarray:
-    """IC weights drawn U[0, hi] per edge (the paper's own weight model, Sec. 5.1)."""
+def _uniform_probabilities(m: int, seed: int, hi: float) -> np.ndarray:
     bg = np.random.PCG64(seed ^ 0x756e69)
-    r = _u32_stream(bg, m).astype(np.float64) / TWO32 * hi
+    return _u32_stream(bg, m).astype(np.float64) / TWO32 * hi
+
+
+def weights_uniform_random(m: int, seed: int, hi: float = 0.1) -> np.ndarray:
+    """IC weights drawn U[0, hi] per edge (the paper's own weight model, Sec. 4.1)."""
+    r = _uniform_probabilities(m, seed, hi)
     return np.minimum(np.floor(r * TWO32 + 0.5), U32_MAX).astype(np.uint32)
+
+
+def weights_uniform_random_lt(in_off: np.ndarray, seed: int, hi: float = 0.1) -> np.ndarray:
+    """LT weights from the same U[0, hi] draws: a vertex whose in-weights sum
+    above 1 has them scaled to sum to 1 (the LT model needs sum <= 1), the
+    others keep them; quantised down so every vertex's sum stays <= 2^32."""
+    m = int(in_off[-1])
+    r = _uniform_probabilities(m, seed, hi)
+    d = np.diff(in_off)
+    owner = np.repeat(np.arange(d.size), d)
+    tot = np.bincount(owner, weights=r, minlength=d.size)
+    scale = 1.0 / np.maximum(tot, 1.0)
+    return np.minimum(np.floor(r * scale[owner] * TWO32), U32_MAX).astype(np.uint32)
 
 
 def rmat_graph(n: int, m: int, seed: int = 42, weights: str = "ic0.1",
@@ -162,7 +179,8 @@ def rmat_graph(n: int, m: int, seed: int = 42, weights: str = "ic0.1",
     """R-MAT graph with one of the weight models used by the workloads.
 
     weights: "ic<p>" (uniform p), "trivalency", "lt" (1/in-degree),
-    "u0.1" (U[0, 0.1] per edge).
+    "u0.1" (IC, U[0, 0.1] per edge), "lt-u0.1" (LT from the same draws, each
+    vertex's in-weights scaled to sum to at most 1).
     """
     src, dst = rmat_edges(n, m, seed=seed, levels=levels)
     in_off, in_src = in_csr(n, src, dst)
@@ -172,6 +190,8 @@ def rmat_graph(n: int, m: int, seed: int = 42, weights: str = "ic0.1",
         w = weights_trivalency(m, seed)
     elif weights == "lt":
         w = weights_inverse_indegree(in_off)
+    elif weights.startswith("lt-u"):
+        w = weights_uniform_random_lt(in_off, seed, float(weights[4:]))
     elif weights.startswith("u"):
         w = weights_uniform_random(m, seed, float(weights[1:]))
     else:

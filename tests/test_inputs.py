@@ -42,3 +42,25 @@ def test_batched_graph_weights_are_inverse_indegree():
     assert np.array_equal(g.w.astype(np.int64), np.minimum(per_v, (1 << 32) - 1))
     sums = np.add.reduceat(g.w.astype(np.int64), g.in_off[:-1][d > 0])
     assert np.all(sums <= 1 << 32)
+
+
+def test_paper_weight_model_uniform_0_to_0_1():
+    """Sec. 4.1: edge probabilities drawn U[0, 0.1].  IC keeps each draw; LT
+    uses the same draws and scales a vertex's in-weights to sum to 1 only when
+    they sum above 1."""
+    g = inputs.rmat_graph(1 << 12, 1 << 16, 5, "u0.1")
+    p = g.w.astype(np.float64) / 2 ** 32
+    assert p.min() >= 0 and p.max() <= 0.1 + 1e-9
+    assert abs(p.mean() - 0.05) < 0.002 and abs(np.median(p) - 0.05) < 0.003
+    assert np.array_equal(inputs.rmat_graph(1 << 12, 1 << 16, 5, "u0.1").w, g.w)
+    lt = inputs.rmat_graph(1 << 12, 1 << 16, 5, "lt-u0.1")
+    assert np.array_equal(lt.in_off, g.in_off) and np.array_equal(lt.in_src, g.in_src)
+    d = np.diff(g.in_off)
+    owner = np.repeat(np.arange(g.n), d)
+    raw = np.bincount(owner, weights=p, minlength=g.n)
+    sums = np.bincount(owner, weights=lt.w.astype(np.float64), minlength=g.n)
+    assert np.all(sums <= 2 ** 32)
+    small = raw <= 1.0                                  # kept: within quantisation
+    assert np.all(np.abs(lt.w.astype(np.float64) - g.w.astype(np.float64))[small[owner]] <= 1.0)
+    big = raw > 1.0                                     # scaled to sum 1
+    assert big.any() and np.all(np.abs(sums[big] / 2 ** 32 - 1.0) < 1e-6)
