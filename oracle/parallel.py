@@ -49,10 +49,16 @@ class Sampler:
             workers = max(1, min(32, os.cpu_count() or 1))
         self.workers = workers
         _O.build()
+        self.pool = None
         self.tmp = tempfile.mkdtemp()
-        path = os.path.join(self.tmp, "graph.npz")
-        np.savez(path, n=np.int64(g.n), in_off=g.in_off, in_src=g.in_src, w=g.w)
-        self.pool = mp.get_context("spawn").Pool(workers, initializer=_init, initargs=(path,))
+        try:
+            path = os.path.join(self.tmp, "graph.npz")
+            np.savez(path, n=np.int64(g.n), in_off=g.in_off, in_src=g.in_src, w=g.w)
+            self.pool = mp.get_context("spawn").Pool(workers, initializer=_init,
+                                                     initargs=(path,))
+        except BaseException:
+            shutil.rmtree(self.tmp, ignore_errors=True)   # no graph file left behind
+            raise
 
     def sample(self, model: int, seed: int, first: int, count: int,
                chunk: int | None = None) -> _O.Pool:

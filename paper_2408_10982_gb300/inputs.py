@@ -77,7 +77,7 @@ def _rmat_lib():
         so = os.path.join(here, "_inputs_rmat.so")
         if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
             tmp = f"{so}.{os.getpid()}.tmp"
-            subprocess.run(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", src, "-o", tmp],
+            subprocess.run(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-pthread", src, "-o", tmp],
                            check=True)
             os.replace(tmp, so)
         lib = ctypes.CDLL(so)
