@@ -84,8 +84,8 @@ def parse():
                     help="RandGreedi as one cooperative launch (1) or two launches (0)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the IC, batched and served sections")
-    ap.add_argument("--served-orkut", action="store_true",
-                    help="served trace with 5%% Orkut-shaped queries (generates a 234M-edge graph)")
+    ap.add_argument("--served-no-orkut", action="store_true",
+                    help="serve the batched mix alone, without the 5%% Orkut-shaped queries")
     return ap.parse_args()
 
 
@@ -388,7 +388,7 @@ def run_ours(args):
         line["cover_paths"] = cover_paths
     if not args.no_extras:
         line["batched"] = bench_batched(im, torch)
-        line["served"] = bench_served(im, torch, args.served_orkut)
+        line["served"] = bench_served(im, torch, not args.served_no_orkut)
         lj = inputs.graph_livejournal_like_both(SEED)
         line["ic"] = bench_ic(im, torch, lj["trivalency"])
         line["imm"] = bench_imm(im, torch, lj["wc"])
@@ -568,17 +568,20 @@ class OneQuery:
         self.im, self.G = im, G
         self.pools = {}
         self.caps = {}
+        self.per_set = {}
 
-    def solve(self, name, model, k, theta, seed):
+    def solve(self, name, model, k, theta, seed, opts=None):
         im = self.im
         p = self.pools.get(name)
+        per = self.per_set.get((name, model), 32.0)     # members per set seen so far
+        want = int(theta * per * 1.25) + 1024
         if p is None:
-            self.caps[name] = (max(theta, 1), max(theta, 1) * 32)
+            self.caps[name] = (max(theta, 1), want)
             p = self.pools[name] = im.Pool(self.G[name], *self.caps[name])
         while True:
             sets, ents = self.caps[name]
-            if theta > sets or theta * 32 > ents:
-                self.caps[name] = (max(sets, theta), max(ents, theta * 32))
+            if theta > sets or want > ents:
+                self.caps[name] = (max(sets, theta), max(ents, want))
                 im.im_pool_reserve(p.handle, *self.caps[name])
             p.reset()
             try:
@@ -590,7 +593,10 @@ class OneQuery:
                 sets, ents = self.caps[name]
                 self.caps[name] = (sets, ents * 4)
                 im.im_pool_reserve(p.handle, *self.caps[name])
-        c = p.cover(k)
+        total = p.info()[1]
+        self.per_set[(name, model)] = max(self.per_set.get((name, model), 0.0),
+                                          total / max(theta, 1))
+        c = p.cover(k, opts)
         return c.seeds, c.coverage
 
     def close(self):
@@ -603,26 +609,39 @@ def _batched_graphs(im):
     return graphs, {name: im.Graph(g) for name, g in graphs.items()}
 
 
+def _mix_opts(im, i, partitions):
+    """Every other query of the mix selects its seeds with RandGreedi (alpha
+    1/4, delta 0.077); partitions 0 leaves the count to the batch."""
+    if i % 2:
+        return None
+    return im.cover_opts(im.IM_RANDGREEDI, partitions, ALPHA, DELTA, SEED, fused=False)
+
+
 def bench_batched(im, torch):
-    """256 queries of the batched mix: one im_solve_batch call versus the
-    one-query path run back to back; results compared query by query."""
+    """256 queries of the batched mix (every other one with RandGreedi, its
+    partition count picked by the batch) in one im_solve_batch call versus the
+    one-query path run back to back with the same counts; results compared
+    query by query."""
     specs = inputs.batched_queries(256, SEED)
     graphs, G = _batched_graphs(im)
-    qlist = [(G[q.graph].handle, q.model, q.k, q.theta, q.seed) for q in specs]
+    qlist = [(G[q.graph].handle, q.model, q.k, q.theta, q.seed, _mix_opts(im, i, 0))
+             for i, q in enumerate(specs)]
     batch = im.im_batch_create()
-    im.im_solve_batch(batch, qlist, 100)                 # warm-up (sizes the arenas)
+    im.im_solve_batch(batch, qlist, 100)          # warm-up: arenas, partition counts
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out = im.im_solve_batch(batch, qlist, 100)
+    out = im.im_solve_batch(batch, qlist, 100, with_partitions=True)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     im.im_batch_destroy(batch)
+    parts = [o[4] for o in out]
     one = OneQuery(im, G)
-    for q in specs[:8]:                                   # warm-up
-        one.solve(q.graph, q.model, q.k, q.theta, q.seed)
+    for i, q in enumerate(specs[:8]):                     # warm-up
+        one.solve(q.graph, q.model, q.k, q.theta, q.seed, _mix_opts(im, i, parts[i]))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain = [one.solve(q.graph, q.model, q.k, q.theta, q.seed) for q in specs]
+    plain = [one.solve(q.graph, q.model, q.k, q.theta, q.seed, _mix_opts(im, i, parts[i]))
+             for i, q in enumerate(specs)]
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
     one.close()
@@ -630,9 +649,13 @@ def bench_batched(im, torch):
     entries = sum(o[3] for o in out)
     for g in G.values():
         g.close()
+    chosen = sorted({p for p in parts if p})
     return {"workload": "256 queries: R-MAT scales 12..18 (edge factor 16), IC (weighted cascade "
-                        "1/in-degree) or LT (1/in-degree), k in [5,100], theta in [2^14,2^20]",
+                        "1/in-degree) or LT (1/in-degree), k in [5,100], theta in [2^14,2^20]; "
+                        "every other query RandGreedi (alpha 1/4, partition count picked by "
+                        "the batch)",
             "queries": len(specs), "sets": sum(q.theta for q in specs), "entries": entries,
+            "randgreedi_queries": sum(1 for p in parts if p), "partition_counts_chosen": chosen,
             "q_per_s": round(len(specs) / t_batch, 2), "ms": round(1000 * t_batch, 2),
             "plain_q_per_s": round(len(specs) / t_plain, 2), "plain_ms": round(1000 * t_plain, 2),
             "speedup_vs_plain": round(t_plain / t_batch, 3), "bit_exact_vs_plain": bool(same)}
@@ -642,38 +665,42 @@ def bench_served(im, torch, orkut: bool):
     """Poisson arrivals (mean 200/s) replayed in real time into im_server
     (continuous batching), versus the one-query path as a FIFO server: each
     query's service time is measured back to back and the trace is replayed
-    through a single queue (done_i = max(arrival_i, done_{i-1}) + service_i)."""
+    through a single queue (done_i = max(arrival_i, done_{i-1}) + service_i).
+    The trace draws from the batched mix (every other mix query RandGreedi with
+    64 parts) plus 5% Orkut-shaped queries (IC p = 0.01, plain greedy)."""
     nq = 512
     specs = inputs.served_trace(nq, SEED, orkut_frac=0.05 if orkut else 0.0)
     graphs, G = _batched_graphs(im)
     if any(q.graph == "orkut" for q in specs):
         G["orkut"] = im.Graph(inputs.graph_orkut_like(SEED))
+    opts = [None if q.graph == "orkut" else _mix_opts(im, i, 64) for i, q in enumerate(specs)]
     srv = im.im_server_create(workers=2, max_batch=8, mem_budget=96 << 30)
-    warm = [im.im_server_submit(srv, G[q.graph].handle, q.model, q.k, q.theta, q.seed)
-            for q in specs[:16]]
+    warm = [im.im_server_submit(srv, G[q.graph].handle, q.model, q.k, q.theta, q.seed, o)
+            for q, o in zip(specs[:16], opts[:16])]
     for t in warm:
         im.im_server_wait(srv, t, 100, 600)
     b0, q0, _ = im.im_server_stats(srv)
     tickets = []
     t0 = time.perf_counter()
-    for q in specs:
+    for q, o in zip(specs, opts):
         delay = q.arrival_s - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
-        tickets.append(im.im_server_submit(srv, G[q.graph].handle, q.model, q.k, q.theta, q.seed))
+        tickets.append(im.im_server_submit(srv, G[q.graph].handle, q.model, q.k, q.theta, q.seed,
+                                           o))
     res = [im.im_server_wait(srv, t, 100, 600) for t in tickets]
     t_all = time.perf_counter() - t0
     b1, q1, _ = im.im_server_stats(srv)
     im.im_server_destroy(srv)
     lat = np.array([r[2] for r in res])
     one = OneQuery(im, G)
-    for q in specs[:8]:
-        one.solve(q.graph, q.model, q.k, q.theta, q.seed)
+    for q, o in zip(specs[:8], opts[:8]):
+        one.solve(q.graph, q.model, q.k, q.theta, q.seed, o)
     torch.cuda.synchronize()
     service, plain = [], []
-    for q in specs:
+    for q, o in zip(specs, opts):
         t1 = time.perf_counter()
-        plain.append(one.solve(q.graph, q.model, q.k, q.theta, q.seed))
+        plain.append(one.solve(q.graph, q.model, q.k, q.theta, q.seed, o))
         torch.cuda.synchronize()
         service.append(time.perf_counter() - t1)
     one.close()
@@ -683,12 +710,15 @@ def bench_served(im, torch, orkut: bool):
         plat.append(1000 * (done - q.arrival_s))
     plat = np.array(plat)
     same = all(a[0].tolist() == b[0].tolist() and a[1] == b[1] for a, b in zip(res, plain))
+    n_ork = sum(1 for q in specs if q.graph == "orkut")
     for g in G.values():
         g.close()
-    return {"workload": f"{nq} Poisson arrivals at 200/s from the batched mix"
-                        + " (im_server: 2 workers, batches of up to 8)"
-                        + (", 5% Orkut-shaped (IC p=0.01, theta in [2^6,2^10])" if orkut else ""),
-            "queries": nq, "span_s": round(specs[-1].arrival_s, 3),
+    return {"workload": f"{nq} Poisson arrivals at 200/s from the batched mix (every other mix "
+                        "query RandGreedi, 64 parts)"
+                        + (f", {n_ork} Orkut-shaped (3,072,441 vertices, 234,369,798 edges, IC "
+                           "p=0.01, theta in [2^6,2^10])" if orkut else "")
+                        + "; im_server: 2 workers, batches of up to 8",
+            "queries": nq, "orkut_queries": n_ork, "span_s": round(specs[-1].arrival_s, 3),
             "q_per_s": round(nq / t_all, 2), "p50_ms": round(float(np.percentile(lat, 50)), 2),
             "p99_ms": round(float(np.percentile(lat, 99)), 2),
             "batches": int(b1 - b0), "mean_batch": round((q1 - q0) / max(b1 - b0, 1), 2),

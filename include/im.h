@@ -246,13 +246,18 @@ im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
  *                       member of every newly covered set; 1, 2, 4, 8, 16 or
  *                       32 runs the lazy greedy of Alg. 2 with that many
  *                       candidates re-evaluated at once (also the width
- *                       IM_GREEDY_LAZY uses; 0 means 16 there). */
+ *                       IM_GREEDY_LAZY uses; 0 means 16 there).
+ *   IM_TUNE_LT_CACHE    one-walk-per-thread LT sampling, L2 policy of its
+ *                       loads: 0 (default) plain; 1 the vertex records stay
+ *                       in L2 ahead of other lines (evict_last); 2 as 1, and
+ *                       the cut points leave L2 first (evict_first). */
 typedef enum {
     IM_TUNE_LT_GROUP = 0,
     IM_TUNE_RG_CLUSTER = 1,
     IM_TUNE_INDEX_REPLICAS = 2,
     IM_TUNE_RG_EVALS = 3,
-    IM_TUNE_GREEDY_EVALS = 4
+    IM_TUNE_GREEDY_EVALS = 4,
+    IM_TUNE_LT_CACHE = 5
 } im_tune_knob;
 im_status im_tune_set(int32_t knob, int64_t value);
 im_status im_tune_get(int32_t knob, int64_t *value);
@@ -427,11 +432,12 @@ im_status im_opim(const im_graph *g, im_model model, int32_t k, double eps, doub
  * its Philox seed.  im_solve_batch solves nq queries in a fixed number of
  * launches (one sampling launch per model over all their samples, one sort,
  * one covering-subset build over all queries' vertices, one greedy launch
- * with one block per query) and gives every query exactly the seeds,
- * gains and coverage that im_sample_rrr + im_max_k_cover (plain greedy) give
- * it alone.  seeds int32[nq * kmax] and gains int64[nq * kmax] (row q: query
- * q's seeds; entries past num_seeds are unspecified; gains may be NULL), host
- * or device; res[nq] host.  An im_batch keeps its device arenas between
+ * with one block per query; RandGreedi queries one after another on the
+ * batch's shared index) and gives every query exactly the seeds, gains and
+ * coverage that im_sample_rrr + im_max_k_cover give it alone.  seeds
+ * int32[nq * kmax] and gains int64[nq * kmax] (row q: query q's seeds;
+ * entries past num_seeds are unspecified; gains may be NULL), host or
+ * device; res[nq] host.  An im_batch keeps its device arenas between
  * calls (grown on demand).  Synchronises the stream. */
 typedef struct {
     const im_graph *graph;
@@ -439,6 +445,16 @@ typedef struct {
     int32_t k;                /* 1 <= k <= min(kmax, n) */
     int64_t theta;
     uint64_t seed;
+    /* SelectSeeds of the query.  All zero: plain greedy.  algo IM_RANDGREEDI:
+     * RandGreedi as im_max_k_cover runs it (two launches; fused ignored), the
+     * same result as im_max_k_cover on the query's own pool.  partitions = 0
+     * there lets the batch pick the partition count: every allowed count (the
+     * powers of two from 16 and the SM count, parts small enough for one
+     * block) is timed on the first query of that graph, model and
+     * power-of-two theta, the fastest is kept for later queries of that kind,
+     * and the count used is reported in im_result.partitions (it changes the
+     * seeds, so a replay passes it explicitly). */
+    im_cover_opts cover;
 } im_query;
 
 typedef struct {
@@ -446,6 +462,8 @@ typedef struct {
     int32_t status;           /* im_status of the query */
     int64_t coverage;
     int64_t entries;          /* RRR set members of the query */
+    int32_t partitions;       /* RandGreedi queries: the partition count used; else 0 */
+    int32_t reserved;
 } im_result;
 
 typedef struct im_batch im_batch;

@@ -16,20 +16,30 @@
 // Each query's result equals what it gets alone (the random stream of a
 // sample depends only on the query's seed and the sample id).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
 
 struct im_batch {
-    int device;
-    void *arena;
-    size_t arena_bytes;
-    void *sscratch;            // sampling scratch
-    size_t sscratch_bytes;
-    int64_t entry_hint;        // members per set seen in earlier batches (x 16)
+    int device = 0;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    void *sscratch = nullptr;  // sampling scratch
+    size_t sscratch_bytes = 0;
+    // members per set to reserve, per graph and model: twice the most seen in
+    // earlier batches (64 before any), four times more after a capacity miss
+    std::map<std::pair<const im_graph *, int32_t>, int64_t> entry_hint;
+    // RandGreedi queries: a pool view per graph (its partition and RandGreedi
+    // buffers are owned, the index is the batch's), and the partition count
+    // picked for each (graph, model, power-of-two theta)
+    std::map<const im_graph *, im_pool *> views;
+    std::map<std::tuple<const im_graph *, int32_t, int32_t>, int32_t> rg_parts;
 };
 
 namespace im {
@@ -54,6 +64,15 @@ __global__ void k_query_bounds(const int64_t *set_off, const int64_t *qset, int3
                                int64_t *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nq; i += gridDim.x * blockDim.x)
         out[i] = set_off[qset[i]];
+}
+
+// A RandGreedi query reads its covering subsets with its own set ids: the
+// batch ids of its entries [vtx_off[0], vtx_off[n]) lose the query's first set.
+__global__ void k_localize(int32_t *set_ids, const int64_t *vtx_off, int64_t n, int64_t sbase) {
+    const int64_t b = vtx_off[0], e = vtx_off[n];
+    for (int64_t t = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < e;
+         t += (int64_t)gridDim.x * blockDim.x)
+        set_ids[t] -= (int32_t)sbase;
 }
 
 __global__ void k_globalize(const int64_t *set_off, int32_t *members, int64_t nsets,
@@ -228,6 +247,40 @@ im_status grow(void **p, size_t *have, size_t need) {
     return IM_OK;
 }
 
+// A pool that borrows a batch's covering subsets for one query at a time:
+// theta, vtx_off and set_ids are set per query; the partition, RandGreedi and
+// scratch buffers are its own, kept between queries on the same graph.
+im_pool *make_pool_view(const im_graph *g, int device) {
+    im_pool *v = new (std::nothrow) im_pool();
+    if (!v) return nullptr;
+    std::memset(v, 0, sizeof(*v));
+    v->g = g;
+    v->device = device;
+    return v;
+}
+
+void release_pool_view(im_pool *v) {
+    if (!v) return;
+    for (void *b : {(void *)v->vtx_cursor, (void *)v->part, (void *)v->part_off,
+                    (void *)v->part_vtx, (void *)v->part_loc, (void *)v->rg_block, v->scratch,
+                    v->res})
+        dev_free(b);
+    delete v;
+}
+
+// The partition counts a RandGreedi query may use: powers of two from 16 and
+// the SM count, each part small enough for one producer block.
+std::vector<int32_t> partition_candidates(int64_t n) {
+    std::vector<int32_t> c;
+    for (int32_t P = 16; P < num_sms(); P *= 2) c.push_back(P);
+    c.push_back(num_sms());
+    std::vector<int32_t> ok;
+    for (int32_t P : c)
+        if (P <= n && (n + P - 1) / P <= 16384) ok.push_back(P);
+    if (ok.empty()) ok.push_back((int32_t)std::min<int64_t>(n, std::max<int64_t>(1, (n + 16383) / 16384)));
+    return ok;
+}
+
 }  // namespace
 }  // namespace im
 
@@ -239,15 +292,15 @@ im_status im_batch_create(im_batch **out) {
     if (!out) return IM_ERR_INVALID_ARG;
     im_batch *b = new (std::nothrow) im_batch();
     if (!b) return IM_ERR_OOM;
-    std::memset(b, 0, sizeof(*b));
     cudaGetDevice(&b->device);
-    b->entry_hint = 64;
     *out = b;
     return IM_OK;
 }
 
 im_status im_batch_destroy(im_batch *b) {
     if (!b) return IM_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    for (auto &kv : b->views) release_pool_view(kv.second);
     cudaFree(b->arena);
     cudaFree(b->sscratch);
     delete b;
@@ -269,6 +322,19 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
             Q.k > Q.graph->n || Q.theta < 0 || Q.theta >= ((int64_t)1 << 31) ||
             Q.graph->device != b->device) {
             set_error("im_solve_batch: query out of range");
+            return IM_ERR_INVALID_ARG;
+        }
+        const im_cover_opts &o = Q.cover;
+        if (o.algo == IM_RANDGREEDI) {
+            if (o.partitions < 0 || o.partitions > 4096 || o.partitions > Q.graph->n ||
+                o.alpha_num < 1 || o.alpha_den < 1 || o.alpha_num > o.alpha_den ||
+                !(o.delta > 0.0 && o.delta < 0.5) ||
+                (o.aggregator != IM_AGG_STREAM && o.aggregator != IM_AGG_GREEDY)) {
+                set_error("im_solve_batch: RandGreedi options out of range");
+                return IM_ERR_INVALID_ARG;
+            }
+        } else if (o.algo != IM_GREEDY_PLAIN && o.algo != IM_GREEDY_LAZY) {
+            set_error("im_solve_batch: unknown algorithm");
             return IM_ERR_INVALID_ARG;
         }
         if (Q.model == IM_LT) {
@@ -314,7 +380,11 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
     const int64_t cov_words = std::max<int64_t>(cb, 1);
 
     for (int attempt = 0; attempt < 8; ++attempt) {
-        const int64_t cap = std::max<int64_t>(1024, sets_total * b->entry_hint);
+        int64_t cap = 1024;
+        for (int32_t q = 0; q < nq; ++q) {
+            auto it = b->entry_hint.find({qs[q].graph, qs[q].model});
+            cap += qs[q].theta * (it == b->entry_hint.end() ? 64 : it->second);
+        }
         // arena layout
         size_t off = 0;
         auto take = [&](size_t bytes) {
@@ -400,12 +470,14 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
             examined += r.examined;
         }
         if (capacity) {
-            b->entry_hint *= 4;
+            for (int32_t q = 0; q < nq; ++q) {
+                auto &h = b->entry_hint[{qs[q].graph, qs[q].model}];
+                h = std::max<int64_t>(h, 64) * 4;
+            }
             continue;
         }
         IM_CUDA(cudaStreamSynchronize(st));
-        b->entry_hint = std::max<int64_t>(b->entry_hint,
-                                          sets_total ? (added * 2 + sets_total - 1) / sets_total : 1);
+
 
         // 2. set offsets and sorted members
         void *tmp = A + o_tmp;
@@ -454,29 +526,34 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
         std::vector<int64_t> hb(nq + 1);
         IM_CUDA(cudaMemcpyAsync(hb.data(), d_bounds, (size_t)(nq + 1) * 8, cudaMemcpyDeviceToHost, st));
         IM_CUDA(cudaStreamSynchronize(st));
-        std::vector<int32_t> by_size(nq);
-        std::iota(by_size.begin(), by_size.end(), 0);
+        // RandGreedi queries (pad 2) run after the greedy launches, one by one
+        std::vector<int32_t> by_size;
+        for (int32_t i = 0; i < nq; ++i)
+            if (qs[order[i]].cover.algo != IM_RANDGREEDI) by_size.push_back(i);
+        const int32_t ng = (int32_t)by_size.size();
         std::sort(by_size.begin(), by_size.end(), [&](int32_t x, int32_t y) {
             return hb[x + 1] - hb[x] > hb[y + 1] - hb[y];
         });
         const double rb = 0.36e9, rg = 17e9, t0 = 0.8e-3;
         const double slots = 2.0 * num_sms();
-        double rest = (double)(hb[nq] - hb[0]), grid_t = 0.0;
-        double best_t = std::max((nq ? (double)(hb[by_size[0] + 1] - hb[by_size[0]]) : 0.0) / rb,
+        double rest = 0.0, grid_t = 0.0;
+        for (int32_t x : by_size) rest += (double)(hb[x + 1] - hb[x]);
+        double best_t = std::max((ng ? (double)(hb[by_size[0] + 1] - hb[by_size[0]]) : 0.0) / rb,
                                  rest / (rb * slots));
         int32_t n_grid = 0;
-        for (int32_t r = 0; r < nq; ++r) {
+        for (int32_t r = 0; r < ng; ++r) {
             const double w = (double)(hb[by_size[r] + 1] - hb[by_size[r]]);
             grid_t += t0 + w / rg;
             rest -= w;
-            const double next = r + 1 < nq ? (double)(hb[by_size[r + 1] + 1] - hb[by_size[r + 1]]) : 0.0;
+            const double next = r + 1 < ng ? (double)(hb[by_size[r + 1] + 1] - hb[by_size[r + 1]]) : 0.0;
             const double t = grid_t + std::max(next / rb, rest / (rb * slots));
             if (t < best_t) {
                 best_t = t;
                 n_grid = r + 1;
             }
         }
-        for (int32_t r = 0; r < nq; ++r) bq[by_size[r]].pad = r < n_grid ? 1 : 0;
+        for (int32_t i = 0; i < nq; ++i) bq[i].pad = 2;
+        for (int32_t r = 0; r < ng; ++r) bq[by_size[r]].pad = r < n_grid ? 1 : 0;
         IM_CUDA(cudaMemcpyAsync(A + o_bq, bq.data(), (size_t)nq * sizeof(BatchQuery),
                                 cudaMemcpyHostToDevice, st));
         int64_t max_nch = 1;
@@ -488,7 +565,7 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
         }
         IM_CUDA(cudaFuncSetAttribute(k_batch_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-        if (n_grid < nq) {
+        if (n_grid < ng) {
             KernelTimer kt(st, "batch_greedy");
             k_batch_greedy<<<(unsigned)std::min<int64_t>(nq, (int64_t)num_sms() * 2), kBGThreads, smem,
                              st>>>((const BatchQuery *)(A + o_bq), nq, vtx_off, set_ids,
@@ -509,6 +586,70 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
                                    d_ns + Q.out, d_cov + Q.out, d_gstatus, st);
             if (s != IM_OK) return s;
         }
+        // RandGreedi queries: each on a view of the batch's index, with its own
+        // set ids; the partition count picked by timing when the query leaves it open
+        std::vector<int32_t> parts_used(nq, 0);
+        for (int32_t i = 0; i < nq; ++i) {
+            const BatchQuery &Q = bq[i];
+            if (Q.pad != 2) continue;
+            const im_query &q = qs[order[i]];
+            {
+                KernelTimer kt(st, "batch_localize");
+                k_localize<<<num_sms() * 4, 256, 0, st>>>(set_ids, vtx_off + Q.vbase, Q.n, Q.sbase);
+            }
+            IM_CUDA(cudaGetLastError());
+            im_pool *&view = b->views[q.graph];
+            if (!view) view = make_pool_view(q.graph, b->device);
+            if (!view) return IM_ERR_OOM;
+            view->theta = Q.theta;
+            view->total = hb[i + 1] - hb[i];
+            view->vtx_off = vtx_off + Q.vbase;
+            view->set_ids = set_ids;
+            view->index_valid = true;
+            im_cover_opts o = q.cover;
+            o.fused = 0;
+            if (o.partitions == 0) {
+                int32_t lg = 0;
+                while (((int64_t)1 << (lg + 1)) <= Q.theta) ++lg;
+                const auto key = std::make_tuple(q.graph, (int32_t)q.model, lg);
+                auto it = b->rg_parts.find(key);
+                if (it == b->rg_parts.end()) {
+                    // time every candidate count (second of two runs) and keep the fastest
+                    cudaEvent_t e0, e1;
+                    IM_CUDA(cudaEventCreate(&e0));
+                    IM_CUDA(cudaEventCreate(&e1));
+                    float best = 0.f;
+                    int32_t bestP = 0;
+                    for (int32_t P : partition_candidates(Q.n)) {
+                        o.partitions = P;
+                        float ms = 0.f;
+                        for (int rep = 0; rep < 2 && s == IM_OK; ++rep) {
+                            cudaEventRecord(e0, st);
+                            s = randgreedi(view, Q.k, &o, d_seeds + Q.out * kmax,
+                                           d_gains + Q.out * kmax, d_ns + Q.out, d_cov + Q.out, st,
+                                           d_gstatus);
+                            cudaEventRecord(e1, st);
+                            cudaEventSynchronize(e1);
+                            cudaEventElapsedTime(&ms, e0, e1);
+                        }
+                        if (s != IM_OK) break;
+                        if (bestP == 0 || ms < best) {
+                            best = ms;
+                            bestP = P;
+                        }
+                    }
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    if (s != IM_OK) return s;
+                    it = b->rg_parts.emplace(key, bestP).first;
+                }
+                o.partitions = it->second;
+            }
+            s = randgreedi(view, Q.k, &o, d_seeds + Q.out * kmax, d_gains + Q.out * kmax,
+                           d_ns + Q.out, d_cov + Q.out, st, d_gstatus);
+            if (s != IM_OK) return s;
+            parts_used[i] = o.partitions;
+        }
         // 5. results
         std::vector<int32_t> hns(nq);
         std::vector<int64_t> hcov(nq);
@@ -526,6 +667,12 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
             res[q].status = IM_OK;
             res[q].coverage = hcov[q];
             res[q].entries = hb[i + 1] - hb[i];
+            res[q].partitions = parts_used[i];
+            res[q].reserved = 0;
+            // the hint for the next batches with this graph and model
+            const int64_t per = qs[q].theta ? (2 * (hb[i + 1] - hb[i]) + qs[q].theta - 1) / qs[q].theta : 1;
+            auto &h = b->entry_hint[{qs[q].graph, qs[q].model}];
+            h = std::max<int64_t>({h, per, 1});
         }
         (void)examined;
         return IM_OK;

@@ -658,8 +658,33 @@ __device__ __forceinline__ bool bloom_has(const uint32_t *bl, uint32_t u) {
             1u) != 0;
 }
 
+// 16-byte read-only load with an L2 eviction-priority policy (createpolicy).
+__device__ __forceinline__ uint4 ldg_policy(const uint4 *p, uint64_t pol) {
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// CP (IM_TUNE_LT_CACHE): 0 plain loads; 1 the vertex records (n x 16 B, read
+// at every step) are kept in L2 ahead of other lines (evict_last); 2 as 1, and
+// the cut points (m x 16 B, mostly single-use) leave L2 first (evict_first).
+template <int CP>
 __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
     extern __shared__ uint32_t bloom[];          // [kBloomWords][kLT1Threads]
+    const uint64_t pol_v = CP >= 1 ? l2_policy_evict_last() : 0ull;
+    const uint64_t pol_c = CP >= 2 ? l2_policy_evict_first() : 0ull;
     const int lane = threadIdx.x & 31;
     uint32_t *bl = bloom + threadIdx.x;
     const int64_t slot0 = (int64_t)blockIdx.x * kLT1Threads + (threadIdx.x & ~31);
@@ -714,12 +739,13 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
         uint32_t u = 0;
         if (active) {
             const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
-            const uint4 vr = __ldg(vrec + cur);
+            const uint4 vr = CP >= 1 ? ldg_policy(vrec + cur, pol_v) : __ldg(vrec + cur);
             const uint32_t d = vr.y;
             int64_t e = -1;
             sbytes += 16u;                           // vertex record
             if (d > 0) {
-                const uint4 gv = __ldg(guide + vr.x + __umulhi(x, d));
+                const uint4 *gp = guide + vr.x + __umulhi(x, d);
+                const uint4 gv = CP >= 2 ? ldg_policy(gp, pol_c) : __ldg(gp);
                 const unsigned long long cum = ((unsigned long long)gv.y << 32) | gv.x;
                 sbytes += 16u;                       // cut point
                 if ((unsigned long long)x < cum) {
@@ -1386,9 +1412,12 @@ im_status run_sampling(const SamplingJob &job, const std::function<im_status(siz
 
     // launch shape: persistent, occupancy-sized
     const int G = model == IM_LT ? (int)tune_value(IM_TUNE_LT_GROUP) : 32;
+    const int lt_cache = (int)tune_value(IM_TUNE_LT_CACHE);
     const bool lt1 = model == IM_LT && G == 1;      // one walk per thread
     const void *kern = model == IM_LT
-                           ? (G == 1    ? (const void *)k_sample_lt1
+                           ? (G == 1    ? (lt_cache == 0   ? (const void *)k_sample_lt1<0>
+                                            : lt_cache == 1 ? (const void *)k_sample_lt1<1>
+                                                            : (const void *)k_sample_lt1<2>)
                               : G == 8  ? (const void *)k_sample_lt<8>
                               : G == 16 ? (const void *)k_sample_lt<16>
                                         : (const void *)k_sample_lt<32>)
@@ -1470,7 +1499,11 @@ im_status run_sampling(const SamplingJob &job, const std::function<im_status(siz
     auto launch = [&](int nblocks, int group) {
         KernelTimer kt(st, model == IM_LT ? "sample_lt" : "sample_ic");
         if (model == IM_LT) {
-            if (group == 1) k_sample_lt1<<<nblocks, kLT1Threads, dyn_smem, st>>>(a);
+            if (group == 1) {
+                if (lt_cache == 0) k_sample_lt1<0><<<nblocks, kLT1Threads, dyn_smem, st>>>(a);
+                else if (lt_cache == 1) k_sample_lt1<1><<<nblocks, kLT1Threads, dyn_smem, st>>>(a);
+                else k_sample_lt1<2><<<nblocks, kLT1Threads, dyn_smem, st>>>(a);
+            }
             else if (group == 8) k_sample_lt<8><<<nblocks, kSampleThreads, 0, st>>>(a);
             else if (group == 16) k_sample_lt<16><<<nblocks, kSampleThreads, 0, st>>>(a);
             else k_sample_lt<32><<<nblocks, kSampleThreads, 0, st>>>(a);

@@ -64,8 +64,13 @@ namespace {
 int64_t footprint(im_server *s, const im_query &q) {
     auto it = s->per_set.find({q.graph, q.model});
     const double per = it != s->per_set.end() ? it->second : 64.0;
+    int64_t rg = 0;
+    if (q.cover.algo == IM_RANDGREEDI) {   // per-part bitmaps and per-set bucket masks
+        const int64_t P = q.cover.partitions > 0 ? q.cover.partitions : 148;
+        rg = P * ((q.theta + 31) / 32) * 4 + q.theta * 8 + q.graph->n * 16;
+    }
     return (int64_t)((double)q.theta * per * 1.5 * 12.0) + q.theta * 20 + q.theta / 8 +
-           q.graph->n * 24 + 4096;
+           q.graph->n * 24 + rg + 4096;
 }
 
 void worker_main(im_server *s) {

@@ -305,13 +305,14 @@ def im_opim(g, model: int, k: int, eps: float, delta: float, seed: int, theta_ca
 class Query(ctypes.Structure):
     """im_query (see include/im.h)."""
     _fields_ = [("graph", ctypes.c_void_p), ("model", ctypes.c_int32), ("k", ctypes.c_int32),
-                ("theta", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+                ("theta", ctypes.c_int64), ("seed", ctypes.c_uint64), ("cover", CoverOpts)]
 
 
 class Result(ctypes.Structure):
     """im_result (see include/im.h)."""
     _fields_ = [("num_seeds", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("coverage", ctypes.c_int64), ("entries", ctypes.c_int64)]
+                ("coverage", ctypes.c_int64), ("entries", ctypes.c_int64),
+                ("partitions", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def im_batch_create():
@@ -324,22 +325,28 @@ def im_batch_destroy(b):
     _check(lib().im_batch_destroy(b), "im_batch_destroy")
 
 
-def im_solve_batch(b, queries, kmax: int, stream=None):
-    """queries: list of (graph handle, model, k, theta, seed).  Returns a list of
-    (seeds, gains, coverage, entries) per query."""
+def im_solve_batch(b, queries, kmax: int, stream=None, with_partitions: bool = False):
+    """queries: list of (graph handle, model, k, theta, seed[, CoverOpts]).
+    Returns a list of (seeds, gains, coverage, entries) per query, with the
+    partition count a RandGreedi query used appended when with_partitions."""
     nq = len(queries)
-    arr = (Query * nq)(*[Query(g.value if hasattr(g, "value") else g, m, k, th, sd)
-                         for g, m, k, th, sd in queries])
+
+    def q(t):
+        g, m, k, th, sd = t[:5]
+        opts = t[5] if len(t) > 5 and t[5] is not None else CoverOpts()
+        return Query(g.value if hasattr(g, "value") else g, m, k, th, sd, opts)
+    arr = (Query * nq)(*[q(t) for t in queries])
     seeds = np.zeros(nq * kmax, np.int32)
     gains = np.zeros(nq * kmax, np.int64)
     res = (Result * nq)()
     _check(lib().im_solve_batch(b, arr, nq, kmax, seeds.ctypes.data, gains.ctypes.data, res,
                                 _stream(stream)), "im_solve_batch")
     out = []
-    for q in range(nq):
-        m = res[q].num_seeds
-        out.append((seeds[q * kmax:q * kmax + m].copy(), gains[q * kmax:q * kmax + m].copy(),
-                    res[q].coverage, res[q].entries))
+    for i in range(nq):
+        m = res[i].num_seeds
+        r = (seeds[i * kmax:i * kmax + m].copy(), gains[i * kmax:i * kmax + m].copy(),
+             res[i].coverage, res[i].entries)
+        out.append(r + (res[i].partitions,) if with_partitions else r)
     return out
 
 
@@ -393,8 +400,10 @@ def im_server_destroy(s):
     _check(lib().im_server_destroy(s), "im_server_destroy")
 
 
-def im_server_submit(s, graph, model: int, k: int, theta: int, seed: int) -> int:
-    q = Query(graph.value if hasattr(graph, "value") else graph, model, k, theta, seed)
+def im_server_submit(s, graph, model: int, k: int, theta: int, seed: int,
+                     opts: CoverOpts | None = None) -> int:
+    q = Query(graph.value if hasattr(graph, "value") else graph, model, k, theta, seed,
+              opts if opts is not None else CoverOpts())
     t = ctypes.c_uint64()
     _check(lib().im_server_submit(s, ctypes.byref(q), ctypes.byref(t)), "im_server_submit")
     return t.value
@@ -479,6 +488,7 @@ IM_TUNE_RG_CLUSTER = 1
 IM_TUNE_INDEX_REPLICAS = 2
 IM_TUNE_RG_EVALS = 3
 IM_TUNE_GREEDY_EVALS = 4
+IM_TUNE_LT_CACHE = 5
 
 
 def im_tune_set(knob: int, value: int):

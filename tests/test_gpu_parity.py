@@ -255,6 +255,19 @@ def test_lt_group_sizes_identical(im, group):
         im.im_tune_set(im.IM_TUNE_LT_GROUP, old)
 
 
+@pytest.mark.parametrize("cache", [0, 1, 2])
+def test_lt_cache_policies_identical(im, cache):
+    """The L2 policy of the LT walk's loads changes no set."""
+    g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+    ref = O.sample(O.LT, g, 5, 0, 40000)
+    im.im_tune_set(im.IM_TUNE_LT_CACHE, cache)
+    try:
+        G, P = gpu_pool(im, g, im.IM_LT, 5, [(0, 40000)], cap_entries=40000 * 512)
+        assert_pool_equal(im, P, ref)
+    finally:
+        im.im_tune_set(im.IM_TUNE_LT_CACHE, 0)
+
+
 @pytest.mark.parametrize("cluster", [-1, 1, 2, 4, 8])
 def test_randgreedi_bucket_stage_variants(im, cluster):
     """Two-launch RandGreedi: every bucket-stage layout (global bitmaps, or a
@@ -328,6 +341,58 @@ def test_solve_batch_matches_oracle_and_single_path(im):
                 assert cov == rc.coverage and entries == pool.members.size
     finally:
         im.im_batch_destroy(batch)
+
+
+def test_solve_batch_randgreedi_queries(im):
+    """Batched RandGreedi queries (plain greedy ones beside them): a fixed
+    partition count, and an open one the batch picks by timing -- every query
+    equals the oracle's RandGreedi with the count the batch reports, and the
+    same query alone through im_max_k_cover."""
+    graphs = {"a": inputs.rmat_graph(1 << 12, 1 << 16, 1, "lt"),
+              "b": inputs.rmat_graph(1 << 13, 1 << 17, 2, "ic0.05"),
+              "c": inputs.rmat_graph(1 << 14, 1 << 18, 3, "lt")}
+    G = {k: im.Graph(g) for k, g in graphs.items()}
+    rg = lambda P, a: im.cover_opts(im.IM_RANDGREEDI, P, a, 0.077, 11, False)
+    specs = [("a", im.IM_LT, 10, 3000, 5, rg(16, (1, 4))),
+             ("b", im.IM_IC, 12, 2500, 6, None),
+             ("c", im.IM_LT, 30, 20000, 7, rg(0, (1, 4))),
+             ("c", im.IM_LT, 20, 18000, 8, rg(0, (1, 2))),
+             ("a", im.IM_LT, 8, 1000, 9, None),
+             ("b", im.IM_IC, 5, 4000, 10, rg(32, (1, 1))),
+             ("c", im.IM_LT, 25, 20000, 11, im.cover_opts(im.IM_RANDGREEDI, 0, (1, 4), 0.077, 11,
+                                                         False, im.IM_AGG_GREEDY))]
+    batch = im.im_batch_create()
+    try:
+        out = im.im_solve_batch(batch, [(G[n].handle, m, k, th, sd, o)
+                                        for n, m, k, th, sd, o in specs], 30,
+                                with_partitions=True)
+    finally:
+        im.im_batch_destroy(batch)
+    for (name, m, k, th, sd, o), (seeds, gains, cov, entries, parts) in zip(specs, out):
+        g = graphs[name]
+        mo = O.IC if m == im.IM_IC else O.LT
+        pool = O.sample(mo, g, sd, 0, th)
+        inv = O.invert(g.n, pool)
+        assert entries == pool.members.size
+        if o is None:
+            r = O.greedy(g.n, pool, inv, k)
+            assert parts == 0
+        else:
+            P = o.partitions or parts
+            assert parts == P and P >= 1
+            r = O.randgreedi(g.n, pool, inv, k, P, 11, O.trunc_count(k, o.alpha_num, o.alpha_den),
+                             0.077, naive=o.aggregator == im.IM_AGG_GREEDY)
+        assert seeds.tolist() == r.seeds.tolist(), name
+        assert gains.tolist() == r.gains.tolist(), name
+        assert cov == r.coverage, name
+        if o is not None:                       # the same query alone
+            Gp, Pp = gpu_pool(im, g, m, sd, [(0, th)], cap_entries=th * 512)
+            alone = Pp.cover(k, im.cover_opts(im.IM_RANDGREEDI, P, (o.alpha_num, o.alpha_den),
+                                              0.077, 11, False, o.aggregator))
+            assert alone.seeds.tolist() == seeds.tolist() and alone.coverage == cov
+            Pp.close()
+    for gh in G.values():
+        gh.close()
 
 
 def test_server_results_equal_alone(im):
