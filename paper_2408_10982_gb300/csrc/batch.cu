@@ -470,8 +470,12 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
             examined += r.examined;
         }
         if (capacity) {
+            std::map<std::pair<const im_graph *, int32_t>, bool> seen;
             for (int32_t q = 0; q < nq; ++q) {
-                auto &h = b->entry_hint[{qs[q].graph, qs[q].model}];
+                const auto key = std::make_pair(qs[q].graph, (int32_t)qs[q].model);
+                if (seen[key]) continue;                 // once per graph and model
+                seen[key] = true;
+                auto &h = b->entry_hint[key];
                 h = std::max<int64_t>(h, 64) * 4;
             }
             continue;
