@@ -271,9 +271,38 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
 // per warp and step.  The queue and visited bitmap (n entries / n bits per
 // block) live in global memory.  The set is copied to the stage by the block.
 constexpr int kICBigThreads = 1024;
+constexpr int kICBigU = 2;          // edge groups per lane in flight (k_sample_ic_big)
 
 // One group of four in-edges of sample s: coins, liveness, visited marks;
 // returns the fresh sources in src[] and their bits.
+// Coins of edge group g (edges 4g .. 4g+3 inside [eb, ee)) from its loaded
+// weights wv and sources sv; marks the live edges' fresh sources visited.
+__device__ __forceinline__ unsigned ic_group_loaded(const uint4 wv, const int4 sv, int64_t g,
+                                                    int64_t eb, int64_t ee, uint32_t s,
+                                                    uint32_t k0, uint32_t k1, uint32_t *vis,
+                                                    int32_t (&src)[4]) {
+    const uint4 coin = philox4x32_10(
+        make_uint4(s, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), kStreamCoin), k0, k1);
+    const uint32_t cv[4] = {coin.x, coin.y, coin.z, coin.w};
+    const uint32_t wq[4] = {wv.x, wv.y, wv.z, wv.w};
+    src[0] = sv.x;
+    src[1] = sv.y;
+    src[2] = sv.z;
+    src[3] = sv.w;
+    unsigned fresh = 0;
+    const int64_t e0 = g << 2;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int64_t e = e0 + c;
+        if (e >= eb && e < ee && cv[c] < wq[c]) {
+            const uint32_t u = (uint32_t)src[c];
+            const uint32_t bit = 1u << (u & 31);
+            if (!(atomicOr(&vis[u >> 5], bit) & bit)) fresh |= 1u << c;
+        }
+    }
+    return fresh;
+}
+
 __device__ __forceinline__ unsigned ic_group(const uint32_t *wgt, const int32_t *in_src, int64_t g,
                                              int64_t eb, int64_t ee, uint32_t s, uint32_t k0,
                                              uint32_t k1, uint32_t *vis, int32_t (&src)[4]) {
@@ -371,25 +400,41 @@ __global__ void __launch_bounds__(kICBigThreads) k_sample_ic_big(SampleArgs a) {
                 const int64_t ng = ee > eb ? ((ee - 1) >> 2) - g0 + 1 : 0;
                 const int64_t incl = warp_incl_scan<int64_t>(ng, lane);
                 const int64_t total = __shfl_sync(kFull, incl, 31);
-                for (int64_t gb = 0; gb < total; gb += 32) {
-                    const int64_t t = gb + lane;
-                    int owner = 0;   // first lane whose inclusive group count exceeds t
+                // kICBigU edge groups per lane in flight: their loads are issued
+                // together before any coin is drawn
+                for (int64_t gb = 0; gb < total; gb += 32 * kICBigU) {
+                    int64_t grp[kICBigU], geb[kICBigU], gee[kICBigU];
+                    uint4 wv[kICBigU];
+                    int4 sv[kICBigU];
 #pragma unroll
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
-                        if (c <= t) owner += step;
+                    for (int u = 0; u < kICBigU; ++u) {
+                        const int64_t t = gb + u * 32 + lane;
+                        int owner = 0;   // first lane whose inclusive group count exceeds t
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
+                            if (c <= t) owner += step;
+                        }
+                        const int64_t o_incl = __shfl_sync(kFull, incl, owner);
+                        const int64_t o_ng = __shfl_sync(kFull, ng, owner);
+                        const int64_t o_g0 = __shfl_sync(kFull, g0, owner);
+                        geb[u] = __shfl_sync(kFull, eb, owner);
+                        gee[u] = __shfl_sync(kFull, ee, owner);
+                        grp[u] = t < total ? o_g0 + (t - (o_incl - o_ng)) : -1;
+                        if (grp[u] >= 0) {
+                            wv[u] = __ldg(reinterpret_cast<const uint4 *>(wgt) + grp[u]);
+                            sv[u] = __ldg(reinterpret_cast<const int4 *>(in_src) + grp[u]);
+                        }
                     }
-                    const int64_t o_incl = __shfl_sync(kFull, incl, owner);
-                    const int64_t o_ng = __shfl_sync(kFull, ng, owner);
-                    const int64_t o_g0 = __shfl_sync(kFull, g0, owner);
-                    const int64_t o_eb = __shfl_sync(kFull, eb, owner);
-                    const int64_t o_ee = __shfl_sync(kFull, ee, owner);
-                    unsigned fresh = 0;
-                    int32_t src[4] = {0, 0, 0, 0};
-                    if (t < total)
-                        fresh = ic_group(wgt, in_src, o_g0 + (t - (o_incl - o_ng)), o_eb, o_ee, s, k0,
-                                         k1, vis, src);
-                    ic_append(fresh, src, lane, &s_tail, q);
+#pragma unroll
+                    for (int u = 0; u < kICBigU; ++u) {
+                        unsigned fresh = 0;
+                        int32_t src[4] = {0, 0, 0, 0};
+                        if (grp[u] >= 0)
+                            fresh = ic_group_loaded(wv[u], sv[u], grp[u], geb[u], gee[u], s, k0, k1,
+                                                    vis, src);
+                        ic_append(fresh, src, lane, &s_tail, q);
+                    }
                 }
             }
             __syncthreads();
