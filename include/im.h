@@ -250,14 +250,25 @@ im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
  *   IM_TUNE_LT_CACHE    one-walk-per-thread LT sampling, L2 policy of its
  *                       loads: 0 (default) plain; 1 the vertex records stay
  *                       in L2 ahead of other lines (evict_last); 2 as 1, and
- *                       the cut points leave L2 first (evict_first). */
+ *                       the cut points leave L2 first (evict_first).
+ *   IM_TUNE_GREEDY_HOT  the standard greedy's decrement kernel keeps exact
+ *                       gains, and looks for the best one, only among the
+ *                       vertices with |S(v)| >= tau = max_v |S(v)| >> value
+ *                       (4 .. 16; default 8); the others keep |S(v)| < tau
+ *                       as a stale bound until the best gain drops below
+ *                       tau, when one pass makes them exact.  0 keeps every
+ *                       gain exact and reads all of them at every step.
+ *                       (Vertices with |S(v)| >= max |S(v)| / 64 always keep
+ *                       their gain as 32 partial counts, spreading the
+ *                       atomics that land on them.) */
 typedef enum {
     IM_TUNE_LT_GROUP = 0,
     IM_TUNE_RG_CLUSTER = 1,
     IM_TUNE_INDEX_REPLICAS = 2,
     IM_TUNE_RG_EVALS = 3,
     IM_TUNE_GREEDY_EVALS = 4,
-    IM_TUNE_LT_CACHE = 5
+    IM_TUNE_LT_CACHE = 5,
+    IM_TUNE_GREEDY_HOT = 6
 } im_tune_knob;
 im_status im_tune_set(int32_t knob, int64_t value);
 im_status im_tune_get(int32_t knob, int64_t *value);

@@ -100,9 +100,9 @@ KernelTimer::~KernelTimer() {
 namespace {
 std::mutex g_tune_mu;
 // IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER, IM_TUNE_INDEX_REPLICAS, IM_TUNE_RG_EVALS,
-// IM_TUNE_GREEDY_EVALS, IM_TUNE_LT_CACHE
-constexpr int kKnobs = 6;
-int64_t g_tune[kKnobs] = {1, 0, 4, 2, 0, 0};
+// IM_TUNE_GREEDY_EVALS, IM_TUNE_LT_CACHE, IM_TUNE_GREEDY_HOT
+constexpr int kKnobs = 7;
+int64_t g_tune[kKnobs] = {1, 0, 4, 2, 0, 0, 8};
 }  // namespace
 
 int64_t tune_value(int32_t knob) {
@@ -620,7 +620,8 @@ im_status im_tune_set(int32_t knob, int64_t value) {
                     (knob == IM_TUNE_GREEDY_EVALS && (value == 0 || value == 1 || value == 2 ||
                                                       value == 4 || value == 8 || value == 16 ||
                                                       value == 32)) ||
-                    (knob == IM_TUNE_LT_CACHE && value >= 0 && value <= 2);
+                    (knob == IM_TUNE_LT_CACHE && value >= 0 && value <= 2) ||
+                    (knob == IM_TUNE_GREEDY_HOT && (value == 0 || (value >= 4 && value <= 16)));
     if (ok) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[knob] = value;
@@ -631,7 +632,7 @@ im_status im_tune_set(int32_t knob, int64_t value) {
 }
 
 im_status im_tune_get(int32_t knob, int64_t *value) {
-    if (!value || knob < IM_TUNE_LT_GROUP || knob > IM_TUNE_LT_CACHE)
+    if (!value || knob < IM_TUNE_LT_GROUP || knob > IM_TUNE_GREEDY_HOT)
         return IM_ERR_INVALID_ARG;
     *value = tune_value(knob);
     return IM_OK;

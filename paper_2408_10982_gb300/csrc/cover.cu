@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -38,6 +39,7 @@ namespace {
 
 constexpr int kGreedyThreads = 512;
 constexpr int kRGThreads = 512;
+constexpr int kProdThreads = 1024;           // producer blocks of the two-launch mode
 constexpr int kBatch = 256;                  // stream slots a consumer reads at once
 constexpr int kUnroll = 8;                   // independent loads in flight per lane in scans
 constexpr int kSpec = 32;                    // largest speculative group of stream elements
@@ -121,7 +123,7 @@ struct GreedyArgs {
     const int64_t *vtx_off;
     const int32_t *set_ids;
     int32_t k;
-    int32_t *counts;                    // [n]
+    int32_t *counts;                    // [n], or [32 ceil(n/32)] with spread
     uint32_t *covered;                  // [ceil(theta/32)]
     unsigned long long *block_best;     // [grid]
     GridBarrier *bar;
@@ -133,9 +135,43 @@ struct GreedyArgs {
     // a query inside a batch: set ids in set_ids and vertex ids in members are
     // offset by sshift and vshift (the query's first set and first vertex)
     int64_t sshift, vshift;
+    // ---- optional (NULL / 0: off), used by the pool's own greedy --------------
+    // counts spread over 32 ceil(n / 32) slots: vertex v at (v mod 32) L + v / 32
+    int32_t spread;
+    // hubs, |S(v)| >= max |S(v)| >> hub_shift (at most hub_cap): each keeps its
+    // gain as kHubRep partial counts, decremented by set id mod kHubRep
+    int32_t *hub_rank;                  // [n] row of a hub, or -1
+    int32_t *hub_cnt;                   // [hub_cap][kHubRep]
+    int32_t *hub_list;                  // [hub_cap] the vertex of each row
+    int32_t *cand;                      // [n] the other vertices with |S(v)| >= tau
+    int32_t *ctl;                       // [4] hub rows, candidates, max |S(v)|, 0
+    int32_t hub_cap, hub_shift, cand_shift;
+    unsigned long long *work;           // [2] per-step chunk counters
 };
 
-__global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
+constexpr int kHubRep = 32;             // partial counts of a hub (one per set id mod 32)
+constexpr int kHubCap = 4096;           // hub rows at most
+constexpr int kHubShift = 6;            // hubs: |S(v)| >= max |S(v)| / 64
+
+// Standard greedy (Sec. 3.2), all k steps in one cooperative launch: a step
+// takes the argmax of the gains (packed gain << 32 | ~v: ties to the smallest
+// id), covers S(v*) on the theta-bit bitmap and decrements the gain of every
+// member of every newly covered set; two grid barriers per step.
+//
+// On graphs with hubs most decrements land on a few vertices, and atomics on
+// one address serialise in its L2 slice: with hub rows, a hub's gain is the
+// sum of kHubRep partial counts, each taking the decrements of the sets whose
+// id is that value mod kHubRep, and the spread layout puts the other
+// high-degree vertices -- low ids on a degree-ordered graph -- in different
+// cache lines.  The argmax reads only the hub rows and the candidate list
+// (|S(v)| >= tau) while the best gain is at least tau, since every other
+// gain is below |S(v)| < tau; those vertices are frozen -- not decremented,
+// keeping |S(v)| as a stale bound -- which skips most decrements (low-degree
+// vertices are most members).  Once the best gain falls below tau, one pass
+// makes the frozen gains exact and every step reads all.
+// Warps take 32-entry chunks of S(v*) from a per-step counter.  Every wait is
+// bounded (grid_sync).
+__global__ void __launch_bounds__(kGreedyThreads, 2) k_greedy(GreedyArgs a) {
     __shared__ unsigned long long shm[33];
     const uint32_t nb = gridDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,20 +179,76 @@ __global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = tid >> 5, nwarps = stride >> 5;
     const int64_t words = (a.theta + 31) / 32;
-    for (int64_t v = tid; v < a.n; v += stride) a.counts[v] = (int32_t)(a.vtx_off[v + 1] - a.vtx_off[v]);
+    const int64_t vwords = (a.n + 31) / 32;
+    const int64_t nslots = a.spread ? 32 * vwords : a.n;
+    auto slot = [&](int64_t v) { return a.spread ? (v & 31) * vwords + (v >> 5) : v; };
+    auto vert = [&](int64_t i) { return a.spread ? (i % vwords) * 32 + i / vwords : i; };
+    unsigned long long lmax = 0;
+    for (int64_t i = tid; i < nslots; i += stride) {
+        const int64_t v = vert(i);
+        const int32_t d = v < a.n ? (int32_t)(a.vtx_off[v + 1] - a.vtx_off[v]) : 0;
+        a.counts[i] = d;
+        lmax = (unsigned long long)d > lmax ? (unsigned long long)d : lmax;
+    }
     for (int64_t x = tid; x < words; x += stride) a.covered[x] = 0u;
+    if (a.hub_rank) {
+        lmax = block_max_u64(lmax, shm);
+        if (threadIdx.x == 0 && lmax) atomicMax(a.ctl + 2, (int32_t)lmax);
+    }
     if (!grid_sync(a.bar, nb, a.status)) return;
+    uint32_t tau = 0;                        // > 0: the argmax reads hubs + candidates
+    int32_t nhub = 0, ncand = 0;
+    if (a.hub_rank) {
+        const uint32_t l = (uint32_t)__ldcg(a.ctl + 2);
+        const uint32_t th = l >> a.hub_shift > 0 ? l >> a.hub_shift : 1;
+        tau = a.cand_shift > 0 ? (l >> a.cand_shift > 0 ? l >> a.cand_shift : 1) : 0;
+        for (int64_t v = tid; v < a.n; v += stride) {
+            const uint32_t d = (uint32_t)(a.vtx_off[v + 1] - a.vtx_off[v]);
+            int32_t r = -1;
+            if (d >= th) {
+                r = atomicAdd(a.ctl + 0, 1);
+                if (r < a.hub_cap) {
+                    a.hub_list[r] = (int32_t)v;
+                    a.hub_cnt[(int64_t)r * kHubRep] = (int32_t)d;
+                    for (int q = 1; q < kHubRep; ++q) a.hub_cnt[(int64_t)r * kHubRep + q] = 0;
+                    a.counts[slot(v)] = 0;   // the row holds the gain
+                } else {
+                    r = -1;
+                }
+            }
+            // below tau a vertex is frozen (-2): its gain stays |S(v)| < tau, a
+            // stale bound, until the best gain drops below tau
+            if (r < 0 && tau > 0) r = d >= tau ? -1 : -2;
+            a.hub_rank[v] = r;
+            if (r == -1 && tau > 0) a.cand[atomicAdd(a.ctl + 1, 1)] = (int32_t)v;
+        }
+        if (!grid_sync(a.bar, nb, a.status)) return;
+        nhub = min(__ldcg(a.ctl + 0), a.hub_cap);
+        ncand = __ldcg(a.ctl + 1);
+    }
     int64_t cov = 0;
     int32_t j = 0;
-    for (; j < a.k; ++j) {
+    while (j < a.k) {
         unsigned long long best = 0;
-        for (int64_t v = tid; v < a.n; v += stride) {
-            const int32_t c = __ldcg(a.counts + v);
+        auto consider = [&](int32_t c, uint32_t v) {
             if (c > 0) {
                 const unsigned long long key =
-                    ((unsigned long long)(uint32_t)c << 32) | (0xffffffffu - (uint32_t)v);
+                    ((unsigned long long)(uint32_t)c << 32) | (0xffffffffu - v);
                 best = key > best ? key : best;
             }
+        };
+        if (tau > 0) {
+            for (int64_t q = tid; q < ncand; q += stride) {
+                const uint32_t v = (uint32_t)__ldcg(a.cand + q);
+                consider(__ldcg(a.counts + slot(v)), v);
+            }
+        } else {
+            for (int64_t i = tid; i < nslots; i += stride)
+                consider(__ldcg(a.counts + i), (uint32_t)vert(i));
+        }
+        for (int64_t h = gwarp; h < nhub; h += nwarps) {      // a hub's gain: its row's sum
+            const int32_t c = warp_sum<int32_t>(__ldcg(a.hub_cnt + h * kHubRep + lane));
+            consider(c, (uint32_t)__ldcg(a.hub_list + h));
         }
         best = block_max_u64(best, shm);
         if (threadIdx.x == 0) a.block_best[blockIdx.x] = best;
@@ -167,6 +259,29 @@ __global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
             gbest = x > gbest ? x : gbest;
         }
         gbest = block_max_u64(gbest, shm);
+        if (tau > 0 && (uint32_t)(gbest >> 32) < tau) {
+            // the best gain fell below tau: the frozen vertices may now win.
+            // Make their gains exact against the sets covered so far, thaw
+            // them, and read every gain from here on (block_best is rewritten
+            // only after the barrier below, when every block has read it)
+            for (int64_t v = gwarp; v < a.n; v += nwarps) {
+                if (__ldcg(a.hub_rank + v) != -2) continue;
+                const int64_t sb = a.vtx_off[v], se = a.vtx_off[v + 1];
+                int miss = 0;
+                for (int64_t t = sb + lane; t < se; t += 32) {
+                    const int64_t il = __ldg(a.set_ids + t) - a.sshift;
+                    miss += !((__ldcg(a.covered + (il >> 5)) >> (il & 31)) & 1u);
+                }
+                miss = warp_sum<int>(miss);
+                if (lane == 0) {
+                    a.counts[slot(v)] = miss;
+                    a.hub_rank[v] = -1;
+                }
+            }
+            tau = 0;
+            if (!grid_sync(a.bar, nb, a.status)) return;
+            continue;
+        }
         if (gbest == 0) break;                       // every remaining gain is zero
         const int32_t vs = (int32_t)(0xffffffffu - (uint32_t)(gbest & 0xffffffffu));
         const int64_t gain = (int64_t)(gbest >> 32);
@@ -176,50 +291,68 @@ __global__ void __launch_bounds__(kGreedyThreads) k_greedy(GreedyArgs a) {
         }
         cov += gain;
         const int64_t sb = a.vtx_off[vs], se = a.vtx_off[vs + 1];
-        for (int64_t base = sb + gwarp * 32; base < se; base += nwarps * 32) {
+        // chunks of S(v*) from this step's counter; the other step's counter
+        // is cleared meanwhile (its last use ended at the previous step's
+        // closing barrier)
+        unsigned long long *work = a.work ? a.work + (j & 1) : nullptr;
+        if (work && blockIdx.x == 0 && threadIdx.x == 0) a.work[(j + 1) & 1] = 0ull;
+        for (int64_t base = sb + gwarp * 32;;) {
+            if (work) {
+                unsigned long long c = 0;
+                if (lane == 0) c = atomicAdd(work, 32ull);
+                base = sb + (int64_t)__shfl_sync(kFull, c, 0);
+            }
+            if (base >= se) break;
             const int64_t t = base + lane;
             int32_t i = -1;
-            bool fresh = false;
-            if (t < se) {
-                i = a.set_ids[t];
-                const int64_t il = i - a.sshift;
-                const uint32_t bit = 1u << (il & 31);
-                fresh = !(atomicOr(&a.covered[il >> 5], bit) & bit);
-            }
-            if (!__any_sync(kFull, fresh)) continue;
-            // decrement the gains of every member of the lane's newly covered
-            // set: the warp walks the concatenation of those member lists 32
-            // entries at a time, several loads in flight per lane
-            int64_t mo = 0, ml = 0;
-            if (fresh) {
-                mo = a.set_off[i];
-                ml = a.set_off[i + 1] - mo;
-            }
-            const int64_t incl = warp_incl_scan<int64_t>(ml, lane);
-            const int64_t tot = __shfl_sync(kFull, incl, 31);
-            constexpr int U = 4;
-            for (int64_t p0 = 0; p0 < tot; p0 += 32 * U) {
-                int32_t mv[U];
-#pragma unroll
-                for (int uu = 0; uu < U; ++uu) {
-                    const int64_t q = p0 + uu * 32 + lane;
-                    int owner = 0;               // first lane whose inclusive count exceeds q
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
-                        if (c <= q) owner += step;
-                    }
-                    const int64_t o_incl = __shfl_sync(kFull, incl, owner);
-                    const int64_t o_ml = __shfl_sync(kFull, ml, owner);
-                    const int64_t o_mo = __shfl_sync(kFull, mo, owner);
-                    mv[uu] = q < tot ? __ldg(a.members + o_mo + (q - (o_incl - o_ml))) : -1;
+            if (t < se) i = a.set_ids[t];
+            const bool fresh = warp_bitmap_set(a.covered, i >= 0 ? i - a.sshift : -1, lane);
+            if (__any_sync(kFull, fresh)) {
+                // decrement the gains of every member of the lane's newly
+                // covered set: the warp walks the concatenation of those
+                // member lists 32 entries at a time, U loads in flight per lane
+                int64_t mo = 0, ml = 0;
+                if (fresh) {
+                    mo = a.set_off[i];
+                    ml = a.set_off[i + 1] - mo;
                 }
+                const int64_t incl = warp_incl_scan<int64_t>(ml, lane);
+                const int64_t tot = __shfl_sync(kFull, incl, 31);
+                constexpr int U = 4;
+                for (int64_t p0 = 0; p0 < tot; p0 += 32 * U) {
+                    int32_t mv[U], ms[U];
 #pragma unroll
-                for (int uu = 0; uu < U; ++uu)
-                    if (mv[uu] >= 0) atomicSub(&a.counts[mv[uu] - a.vshift], 1);
+                    for (int uu = 0; uu < U; ++uu) {
+                        const int64_t q = p0 + uu * 32 + lane;
+                        int owner = 0;           // first lane whose inclusive count exceeds q
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const int64_t c = __shfl_sync(kFull, incl, owner + step - 1);
+                            if (c <= q) owner += step;
+                        }
+                        const int64_t o_incl = __shfl_sync(kFull, incl, owner);
+                        const int64_t o_ml = __shfl_sync(kFull, ml, owner);
+                        const int64_t o_mo = __shfl_sync(kFull, mo, owner);
+                        ms[uu] = __shfl_sync(kFull, i, owner);
+                        mv[uu] = q < tot ? __ldg(a.members + o_mo + (q - (o_incl - o_ml))) : -1;
+                    }
+#pragma unroll
+                    for (int uu = 0; uu < U; ++uu) {
+                        if (mv[uu] < 0) continue;
+                        const int64_t u = mv[uu] - a.vshift;
+                        const int32_t hr = a.hub_rank ? __ldcg(a.hub_rank + u) : -1;
+                        if (hr >= 0)
+                            red_add_s32(a.hub_cnt + (int64_t)hr * kHubRep + (ms[uu] & (kHubRep - 1)),
+                                        -1);
+                        else if (hr == -1)
+                            red_add_s32(a.counts + slot(u), -1);   // -2: frozen
+                    }
+                }
             }
+            if (!work) base += nwarps * 32;
         }
         if (!grid_sync(a.bar, nb, a.status)) return;
+        ++j;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *a.nseeds = j;
@@ -586,6 +719,14 @@ __device__ void consume(const RGArgs &a, int b, long long *shs) {
         }
     }
     __syncthreads();
+}
+
+// The producers alone (two-launch mode): one block of kProdThreads per part.
+__global__ void __launch_bounds__(kProdThreads) k_rg_local(RGArgs a) {
+    extern __shared__ int32_t key[];
+    __shared__ unsigned long long shm[33];
+    __shared__ long long shs[33];
+    for (int p = blockIdx.x; p < a.P; p += gridDim.x) produce(a, p, key, shm, shs);
 }
 
 __global__ void __launch_bounds__(kRGThreads) k_randgreedi(RGArgs a) {
@@ -1059,16 +1200,25 @@ im_status greedy_plain(im_pool *p, int32_t k, int32_t *d_seeds, int64_t *d_gains
         off += (bytes + 255) & ~(size_t)255;
         return at;
     };
-    const size_t o_cnt = take((size_t)n * 4), o_cov = take((size_t)std::max<int64_t>(words, 1) * 4),
-                 o_best = take((size_t)grid * 8), o_bar = take(sizeof(GridBarrier));
+    const int32_t cand_shift = (int32_t)tune_value(IM_TUNE_GREEDY_HOT);
+    const int64_t vwords = (n + 31) / 32;
+    const size_t o_cnt = take((size_t)vwords * 32 * 4),
+                 o_cov = take((size_t)std::max<int64_t>(words, 1) * 4),
+                 o_best = take((size_t)grid * 8), o_bar = take(sizeof(GridBarrier)),
+                 o_work = take(16), o_hrank = take((size_t)n * 4),
+                 o_hcnt = take((size_t)kHubCap * kHubRep * 4), o_hlist = take((size_t)kHubCap * 4),
+                 o_cand = take((size_t)n * 4), o_ctl = take(16);
     void *base = nullptr;
     im_status s = pool_scratch(p, off, &base);
     if (s != IM_OK) return s;
     char *B = (char *)base;
     IM_CUDA(cudaMemsetAsync(B + o_bar, 0, sizeof(GridBarrier), st));
+    IM_CUDA(cudaMemsetAsync(B + o_work, 0, 16, st));
+    IM_CUDA(cudaMemsetAsync(B + o_ctl, 0, 16, st));
     IM_CUDA(cudaMemsetAsync(d_nseeds, 0, sizeof(int32_t), st));
     IM_CUDA(cudaMemsetAsync(d_cov, 0, sizeof(int64_t), st));
     GreedyArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.n = n;
     a.theta = theta;
     a.set_off = p->set_off;
@@ -1085,8 +1235,16 @@ im_status greedy_plain(im_pool *p, int32_t k, int32_t *d_seeds, int64_t *d_gains
     a.nseeds = d_nseeds;
     a.coverage = d_cov;
     a.status = d_status;
-    a.sshift = 0;
-    a.vshift = 0;
+    a.spread = 1;
+    a.hub_rank = (int32_t *)(B + o_hrank);
+    a.hub_cnt = (int32_t *)(B + o_hcnt);
+    a.hub_list = (int32_t *)(B + o_hlist);
+    a.cand = (int32_t *)(B + o_cand);
+    a.ctl = (int32_t *)(B + o_ctl);
+    a.hub_cap = kHubCap;
+    a.hub_shift = kHubShift;
+    a.cand_shift = cand_shift;
+    a.work = (unsigned long long *)(B + o_work);
     void *args[] = {&a};
     KernelTimer kt(st, "greedy");
     IM_CUDA(cudaLaunchCooperativeKernel((const void *)k_greedy, dim3(grid), dim3(kGreedyThreads),
@@ -1120,6 +1278,7 @@ im_status greedy_launch_view(int64_t n, int64_t theta, const int64_t *set_off,
     if (per_sm < 1) return IM_ERR_UNSUPPORTED;
     const int grid = std::min(per_sm * num_sms(), max_grid);
     GreedyArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.n = n;
     a.theta = theta;
     a.set_off = set_off;
@@ -1312,12 +1471,18 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
                                             prod_smem, st));
     } else {
         // producers alone, then consumers alone (the stream is complete by then)
-        a.nprod = std::min<int32_t>(P, resident);
+        IM_CUDA(cudaFuncSetAttribute(k_rg_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)prod_smem));
+        int per_l = 0;
+        IM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, k_rg_local, kProdThreads,
+                                                              prod_smem));
+        if (per_l < 1) return IM_ERR_UNSUPPORTED;
+        a.nprod = std::min<int32_t>(P, per_l * num_sms());
         a.ncons = 0;
         a.first_role = 0;
         {
             KernelTimer kt(st, "randgreedi_local");
-            k_randgreedi<<<a.nprod, kRGThreads, prod_smem, st>>>(a);
+            k_rg_local<<<a.nprod, kProdThreads, prod_smem, st>>>(a);
         }
         IM_CUDA(cudaGetLastError());
         const int64_t want = tune_value(IM_TUNE_RG_CLUSTER);   // 0 auto, -1 off, 1..8

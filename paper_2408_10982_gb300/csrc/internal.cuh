@@ -62,6 +62,10 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Fire-and-forget add to global memory (no value returned).
+__device__ __forceinline__ void red_add_s32(int32_t *p, int32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -139,6 +143,31 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
+}
+
+// Sets bit `id` of a bitmap for every lane with id >= 0 (all 32 lanes call
+// it) and returns whether the lane's bit was clear before.  Lanes whose bits
+// share a word combine them first, so a run of nearby ids -- S(v) lists are
+// close to ascending -- costs one atomic per word instead of one per id.
+__device__ __forceinline__ bool warp_bitmap_set(uint32_t *bits, int64_t id, int lane) {
+    const uint32_t w = id >= 0 ? (uint32_t)(id >> 5) : 0xffffffffu;
+    const uint32_t bit = id >= 0 ? 1u << (id & 31) : 0u;
+    const unsigned grp = __match_any_sync(kFull, w);
+    const uint32_t all = __reduce_or_sync(grp, bit);
+    const int leader = __ffs(grp) - 1;
+    uint32_t old = 0;
+    if (lane == leader && id >= 0) old = atomicOr(bits + w, all);
+    old = __shfl_sync(grp, old, leader);
+    return id >= 0 && !(old & bit);
+}
+
+// The same without the answer (a reduction instead of a returning atomic).
+__device__ __forceinline__ void warp_bitmap_or(uint32_t *bits, int64_t id, int lane) {
+    const uint32_t w = id >= 0 ? (uint32_t)(id >> 5) : 0xffffffffu;
+    const uint32_t bit = id >= 0 ? 1u << (id & 31) : 0u;
+    const unsigned grp = __match_any_sync(kFull, w);
+    const uint32_t all = __reduce_or_sync(grp, bit);
+    if (lane == __ffs(grp) - 1 && id >= 0) atomicOr(bits + w, all);
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {

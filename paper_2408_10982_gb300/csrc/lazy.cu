@@ -508,9 +508,9 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_greedy_lazy(LazyArgs a) {
         }
         // ---- cover S(v*) over the whole grid
         const int64_t sb = __ldg(a.vtx_off + vs), se = __ldg(a.vtx_off + vs + 1);
-        for (int64_t t = sb + gtid; t < se; t += stride) {
-            const int32_t id = __ldg(a.set_ids + t);
-            atomicOr(a.covered + (id >> 5), 1u << (id & 31));
+        for (int64_t base = sb + (gtid & ~(int64_t)31); base < se; base += stride) {
+            const int64_t t = base + lane;
+            warp_bitmap_or(a.covered, t < se ? (int64_t)__ldg(a.set_ids + t) : -1, lane);
         }
         if (!grid_sync(a.bar, nb, a.status)) return;
     }

@@ -489,6 +489,7 @@ IM_TUNE_INDEX_REPLICAS = 2
 IM_TUNE_RG_EVALS = 3
 IM_TUNE_GREEDY_EVALS = 4
 IM_TUNE_LT_CACHE = 5
+IM_TUNE_GREEDY_HOT = 6
 
 
 def im_tune_set(knob: int, value: int):

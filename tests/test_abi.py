@@ -52,7 +52,7 @@ def _no_gpu():
 
 
 def test_tuning_knobs_defaults_values_and_rejections(libpath):
-    """The knob values include/im.h documents: defaults 1, 0, 4, 2, 0, 0; every
+    """The knob values include/im.h documents: defaults 1, 0, 4, 2, 0, 0, 8; every
     allowed value is stored; anything else is IM_ERR_INVALID_ARG and leaves
     the knob unchanged."""
     from paper_2408_10982_gb300 import im
@@ -61,10 +61,12 @@ def test_tuning_knobs_defaults_values_and_rejections(libpath):
                im.IM_TUNE_INDEX_REPLICAS: [1, 2, 4, 8],
                im.IM_TUNE_RG_EVALS: [1, 2, 4, 8],
                im.IM_TUNE_GREEDY_EVALS: [0, 1, 2, 4, 8, 16, 32],
-               im.IM_TUNE_LT_CACHE: [0, 1, 2]}
+               im.IM_TUNE_LT_CACHE: [0, 1, 2],
+               im.IM_TUNE_GREEDY_HOT: [0, 4, 8, 12, 16]}
     defaults = {im.IM_TUNE_LT_GROUP: 1, im.IM_TUNE_RG_CLUSTER: 0,
                 im.IM_TUNE_INDEX_REPLICAS: 4, im.IM_TUNE_RG_EVALS: 2,
-                im.IM_TUNE_GREEDY_EVALS: 0, im.IM_TUNE_LT_CACHE: 0}
+                im.IM_TUNE_GREEDY_EVALS: 0, im.IM_TUNE_LT_CACHE: 0,
+                im.IM_TUNE_GREEDY_HOT: 8}
     before = {k: im.im_tune_get(k) for k in allowed}
     try:
         for k in allowed:
@@ -74,15 +76,15 @@ def test_tuning_knobs_defaults_values_and_rejections(libpath):
                 im.im_tune_set(k, v)
                 assert im.im_tune_get(k) == v
             keep = im.im_tune_get(k)
-            for bad in (0 if k not in (im.IM_TUNE_RG_CLUSTER, im.IM_TUNE_LT_CACHE) else 3, 3, 5, 64,
-                        -2, 1 << 40):
+            for bad in (0 if k not in (im.IM_TUNE_RG_CLUSTER, im.IM_TUNE_LT_CACHE,
+                                       im.IM_TUNE_GREEDY_HOT) else 3, 3, 17, 64, -2, 1 << 40):
                 if bad in vals:
                     continue
                 with pytest.raises(im.ImError) as e:
                     im.im_tune_set(k, bad)
                 assert e.value.status == im.IM_ERR_INVALID_ARG
                 assert im.im_tune_get(k) == keep
-        for bad_knob in (-1, 6, 99):
+        for bad_knob in (-1, 7, 99):
             with pytest.raises(im.ImError):
                 im.im_tune_set(bad_knob, 1)
             with pytest.raises(im.ImError):

@@ -125,3 +125,27 @@ def test_randgreedi_naive_rejects_bad_aggregator(im):
     with pytest.raises(im.ImError) as e:
         P.cover(4, opts)
     assert e.value.status == im.IM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shift", [0, 4, 8, 16])
+def test_greedy_hot_vertex_threshold(im, shift):
+    """The standard greedy with exact gains kept only for vertices with
+    |S(v)| >= max |S(v)| >> shift: the seeds equal the oracle's, including
+    instances whose best gain falls below that bound (tau = l/16 on k = 100
+    picks), where the stale gains are made exact midway."""
+    im.im_tune_set(im.IM_TUNE_GREEDY_HOT, shift)
+    try:
+        cases = [(inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt"), im.IM_LT, 20000, 100),
+                 (inputs.graph_small_ic(), im.IM_IC, 16384, 16),
+                 (inputs.rmat_graph(1 << 12, 1 << 16, 3, "lt"), im.IM_LT, 40, 50)]
+        for g, model, theta, k in cases:
+            G, P = gpu_pool(im, g, model, 7, [(0, theta)], cap_entries=theta * 1024)
+            ref = O.sample(O.IC if model == im.IM_IC else O.LT, g, 7, 0, theta)
+            rc = O.greedy(g.n, ref, O.invert(g.n, ref), k)
+            c = P.cover(k)
+            assert c.seeds.tolist() == rc.seeds.tolist() and c.gains.tolist() == rc.gains.tolist()
+            assert c.coverage == rc.coverage
+            P.close()
+            G.close()
+    finally:
+        im.im_tune_set(im.IM_TUNE_GREEDY_HOT, 8)
