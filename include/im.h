@@ -281,11 +281,14 @@ im_status im_tune_get(int32_t knob, int64_t *value);
  * its bucket-stage layout, with rg_opts' partition count, alpha and delta.
  * Results never depend on these knobs, so tuning changes only speed; the
  * partition count itself is a parameter of the method and is not tuned.
- *   out->lt_group, index_replicas, rg_evals, rg_cluster: the chosen values
- *       (-1 where not tuned);
+ * Also tried: the L2 policy of the one-walk-per-thread LT sampler (LT with
+ * one lane per walk) and the standard greedy's tau (IM_TUNE_GREEDY_HOT).
+ *   out->lt_group, index_replicas, rg_evals, rg_cluster, lt_cache,
+ *       greedy_hot: the chosen values (-1 where not tuned);
  *   out->ms[row][i]: the best-of-two time of the i-th value tried (rows: LT
  *       group {1, 8, 16, 32}, replicas {1, 2, 4, 8}, evaluation width
- *       {1, 2, 4, 8}, bucket stage {0, 1, 2, 4, 8, -1}); -1 where not run.
+ *       {1, 2, 4, 8}, bucket stage {0, 1, 2, 4, 8, -1}, LT cache {0, 1, 2},
+ *       greedy tau {0, 7, 8, 10}); -1 where not run.
  * Allocates a probe pool (and a small result buffer) and frees them before it
  * returns.  Synchronises the stream. */
 typedef struct {
@@ -293,7 +296,9 @@ typedef struct {
     int32_t index_replicas;
     int32_t rg_evals;
     int32_t rg_cluster;
-    double ms[4][8];
+    int32_t lt_cache;
+    int32_t greedy_hot;
+    double ms[6][8];
 } im_tune_result;
 im_status im_autotune(const im_graph *g, im_model model, uint64_t seed, int64_t theta, int32_t k,
                       const im_cover_opts *rg_opts, im_tune_result *out, void *stream);

@@ -61,10 +61,10 @@ extern "C" im_status im_autotune(const im_graph *g, im_model model, uint64_t see
     }
     DeviceGuard dg(g->device);
     cudaStream_t st = as_stream(stream);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 8; ++j) out->ms[i][j] = -1.0;
     out->lt_group = out->rg_evals = out->rg_cluster = -1;
-    out->index_replicas = -1;
+    out->index_replicas = out->lt_cache = out->greedy_hot = -1;
     // the probe pool: grow the member capacity until the sample fits
     int64_t cap = theta * 64;
     im_pool *p = nullptr;
@@ -107,6 +107,13 @@ extern "C" im_status im_autotune(const im_graph *g, im_model model, uint64_t see
             return time_best(st, [&]() { return resample(); }, &err);
         });
     }
+    // L2 policy of the one-walk-per-thread LT sampler
+    if (model == IM_LT && out->lt_group == 1) {
+        const int64_t v[3] = {0, 1, 2};
+        out->lt_cache = pick(IM_TUNE_LT_CACHE, v, 3, 4, [&]() {
+            return time_best(st, [&]() { return resample(); }, &err);
+        });
+    }
     // counter replicas of the covering-subset build
     {
         const int64_t v[4] = {1, 2, 4, 8};
@@ -116,6 +123,25 @@ extern "C" im_status im_autotune(const im_graph *g, im_model model, uint64_t see
                 return r != IM_OK ? r : im_pool_index(p, stream);
             }, &err);
         });
+    }
+    // the standard greedy's tau
+    if (err == IM_OK) {
+        s = im_pool_index(p, stream);
+        int32_t *d = nullptr;
+        if (s == IM_OK && cudaMalloc(&d, (size_t)k * 16 + 64) != cudaSuccess) s = IM_ERR_OOM;
+        if (s == IM_OK) {
+            int32_t *seeds = d;
+            int64_t *gains = (int64_t *)((char *)d + (((size_t)k * 4 + 15) & ~(size_t)15));
+            int32_t *ns = (int32_t *)(gains + k);
+            int64_t *cov = (int64_t *)((char *)ns + 16);
+            const int64_t v[4] = {0, 7, 8, 10};
+            out->greedy_hot = pick(IM_TUNE_GREEDY_HOT, v, 4, 5, [&]() {
+                return time_best(st, [&]() {
+                    return im_max_k_cover(p, k, nullptr, seeds, gains, ns, cov, stream);
+                }, &err);
+            });
+            cudaFree(d);
+        }
     }
     // RandGreedi: local-greedy evaluation width, bucket-stage layout
     if (rg_opts && rg_opts->algo == IM_RANDGREEDI && err == IM_OK) {

@@ -368,7 +368,8 @@ class TuneResult(ctypes.Structure):
     """im_tune_result (see include/im.h)."""
     _fields_ = [("lt_group", ctypes.c_int32), ("index_replicas", ctypes.c_int32),
                 ("rg_evals", ctypes.c_int32), ("rg_cluster", ctypes.c_int32),
-                ("ms", (ctypes.c_double * 8) * 4)]
+                ("lt_cache", ctypes.c_int32), ("greedy_hot", ctypes.c_int32),
+                ("ms", (ctypes.c_double * 8) * 6)]
 
 
 def im_autotune(g, model: int, seed: int, theta: int, k: int, rg_opts: CoverOpts | None = None,
@@ -380,7 +381,8 @@ def im_autotune(g, model: int, seed: int, theta: int, k: int, rg_opts: CoverOpts
                              None if rg_opts is None else ctypes.byref(rg_opts), ctypes.byref(r),
                              _stream(stream)), "im_autotune")
     return {"lt_group": r.lt_group, "index_replicas": r.index_replicas, "rg_evals": r.rg_evals,
-            "rg_cluster": r.rg_cluster, "ms": [[round(x, 3) for x in row] for row in r.ms]}
+            "rg_cluster": r.rg_cluster, "lt_cache": r.lt_cache, "greedy_hot": r.greedy_hot,
+            "ms": [[round(x, 3) for x in row] for row in r.ms]}
 
 
 class ServerOpts(ctypes.Structure):

@@ -515,7 +515,7 @@ def test_autotune_picks_allowed_values_and_keeps_results(im):
     """im_autotune times the result-invariant knobs on a probe and leaves the
     fastest values set; the pool and both covers still equal the oracle's."""
     knobs = (im.IM_TUNE_LT_GROUP, im.IM_TUNE_RG_CLUSTER, im.IM_TUNE_INDEX_REPLICAS,
-             im.IM_TUNE_RG_EVALS)
+             im.IM_TUNE_RG_EVALS, im.IM_TUNE_LT_CACHE, im.IM_TUNE_GREEDY_HOT)
     saved = [im.im_tune_get(kn) for kn in knobs]
     try:
         g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
@@ -527,11 +527,20 @@ def test_autotune_picks_allowed_values_and_keeps_results(im):
         assert im.im_tune_get(im.IM_TUNE_LT_GROUP) == r["lt_group"]
         assert im.im_tune_get(im.IM_TUNE_RG_CLUSTER) == r["rg_cluster"]
         assert all(x >= 0 for x in r["ms"][0][:4]) and all(x >= 0 for x in r["ms"][3][:6])
+        assert r["greedy_hot"] in (0, 7, 8, 10) and all(x >= 0 for x in r["ms"][5][:4])
+        assert im.im_tune_get(im.IM_TUNE_GREEDY_HOT) == r["greedy_hot"]
+        assert r["lt_cache"] in (-1, 0, 1, 2)
+        if r["lt_group"] == 1:
+            assert r["lt_cache"] in (0, 1, 2) and all(x >= 0 for x in r["ms"][4][:3])
         _rg_compare(im, g, im.IM_LT, 30000, 50, 148, (1, 4), 0.077, False)
+        c = gpu_pool(im, g, im.IM_LT, 42, [(0, 20000)])[1].cover(50)
+        ref = O.sample(O.LT, g, 42, 0, 20000)
+        rc = O.greedy(g.n, ref, O.invert(g.n, ref), 50)
+        assert c.seeds.tolist() == rc.seeds.tolist() and c.coverage == rc.coverage
         G2, P2 = gpu_pool(im, g, im.IM_LT, 7, [(0, 20000)])
         assert_pool_equal(im, P2, O.sample(O.LT, g, 7, 0, 20000))
         r_ic = im.im_autotune(G.handle, im.IM_IC, 3, 5000, 10)
-        assert r_ic["lt_group"] == -1 and r_ic["rg_evals"] == -1
+        assert r_ic["lt_group"] == -1 and r_ic["rg_evals"] == -1 and r_ic["lt_cache"] == -1
     finally:
         for kn, v in zip(knobs, saved):
             im.im_tune_set(kn, v)
