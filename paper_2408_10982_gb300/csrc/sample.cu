@@ -559,11 +559,12 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
         const uint4 vr = active ? __ldg(vrec + cur) : make_uint4(0u, 0u, 0u, 0u);
         const int32_t d = (int32_t)vr.y;
         bool live = active && d > 0;                 // group-uniform
-        const int lmax = (int)__reduce_max_sync(kFull, live ? vr.w : 0u);
-        const unsigned long long *lvl = tree + vr.z;   // levels stored top-down
+        const uint32_t nlev = vr.z >> 28;
+        const int lmax = (int)__reduce_max_sync(kFull, live ? nlev : 0u);
+        const unsigned long long *lvl = tree + (vr.z & 0x0fffffffu);   // levels stored top-down
         int32_t blk = 0;
         for (int l = lmax; l >= 1; --l) {
-            const bool here = live && l <= (int)vr.w;
+            const bool here = live && l <= (int)nlev;
             const int32_t sz = here ? (int32_t)(((int64_t)d + (1ll << (5 * l)) - 1) >> (5 * l)) : 0;
             int lf = NV;
 #pragma unroll
@@ -674,9 +675,10 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
 }
 
 // LT, one walk per thread.  A step is one Philox draw, the vertex record and
-// one guide entry (see k_lt_guide): two dependent loads for any in-degree,
-// with a binary search over the running sums only when the draw lies past
-// the guide's edge.  The revisit test goes through a 1024-bit Bloom filter of
+// one dependent load: the source of in-edge floor(x / u) when all in-edges of
+// the vertex weigh u (1/in-degree weights, for one), else one guide entry (see
+// k_lt_guide), with a binary search over the running sums only when the draw
+// lies past the guide's edge.  The revisit test goes through a 1024-bit Bloom filter of
 // the walk in shared memory (two hashes); only a hit is checked exactly, by
 // the whole warp scanning that walk's path.  Finished walks are copied to the
 // stage by the whole warp as well, after one warp-wide reservation.
@@ -739,6 +741,7 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
     uint32_t s = 0, cur = 0, k0 = 0, k1 = 0;
     const uint4 *vrec = nullptr, *guide = nullptr;
     const unsigned long long *leaf = nullptr;
+    const int32_t *srcs = nullptr;
     int32_t len = 0;
     unsigned long long sexam = 0, exam = 0, abytes = 0;
     uint32_t sbytes = 0;
@@ -760,6 +763,7 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
                     vrec = V.lt_vrec;
                     guide = V.lt_guide;
                     leaf = V.lt_leaf;
+                    srcs = V.in_src;
                     k0 = seed_lo(V.seed);
                     k1 = seed_hi(V.seed);
                     s = V.first + (uint32_t)(j - __ldg(a.qstart + qi));
@@ -788,7 +792,14 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
             const uint32_t d = vr.y;
             int64_t e = -1;
             sbytes += 16u;                           // vertex record
-            if (d > 0) {
+            if (vr.w != 0u) {                        // equal in-weights u: edge floor(x / u)
+                const uint32_t ei = x / vr.w;
+                if (ei < d) {
+                    e = ei;
+                    u = (uint32_t)__ldg(srcs + vr.x + ei);
+                    sbytes += 4u;                    // source of the pick
+                }
+            } else if (d > 0) {
                 const uint4 *gp = guide + vr.x + __umulhi(x, d);
                 const uint4 gv = CP >= 2 ? ldg_policy(gp, pol_c) : __ldg(gp);
                 const unsigned long long cum = ((unsigned long long)gv.y << 32) | gv.x;
@@ -893,7 +904,12 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
     if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
 }
 
-// LT search index.  vrec[v] = {eb, d, tree offset, number of upper levels L}.
+// LT search index.  vrec[v] = {eb, d, tree offset | L << 28, u} with L the
+// number of upper tree levels (tree offsets stay below 2^28 since m < 2^31) and
+// u the common weight of v's in-edges when they all carry the same nonzero
+// weight (0 otherwise).  For such a vertex the pick needs no table: the running
+// sum of edge i is (i + 1) u, so a draw x picks edge floor(x / u) when that is
+// below d and nothing otherwise.
 // For vertex v with in-edges [eb, eb + d):
 //   leaf[e] = (sum of w over v's in-edges up to and including e) << 31 | src(e)
 // (the running sum is at most 2^32 for valid LT weights -- 33 bits -- and
@@ -936,12 +952,16 @@ __global__ void k_lt_index_small(const int64_t *in_off, const int32_t *in_src, c
         const int64_t b = in_off[v], e = in_off[v + 1], d = e - b;
         if (d > 32) continue;   // k_lt_index
         unsigned long long c = 0;
+        const uint32_t w0 = d > 0 ? w[b] : 0u;
+        bool same = true;
         for (int64_t i = b; i < e; ++i) {
-            c += (unsigned long long)w[i];
+            const uint32_t wi = w[i];
+            same &= wi == w0;
+            c += (unsigned long long)wi;
             leaf[i] = (c << 31) | (unsigned long long)(uint32_t)in_src[i];
         }
         if (c > (1ull << 32)) atomicExch(invalid, 1);
-        vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], 0u);
+        vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], same ? w0 : 0u);
     }
 }
 
@@ -957,18 +977,24 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
         const int64_t b = in_off[v], e = in_off[v + 1], d = e - b;
         if (d <= 32 || d > kLtBlockDeg) continue;   // k_lt_index_small, k_lt_index_block
         unsigned long long carry = 0;
+        const uint32_t w0 = w[b];
+        bool same = true;
         for (int64_t base = b; base < e; base += 32) {
             const int64_t i = base + lane;
-            const unsigned long long x = i < e ? (unsigned long long)w[i] : 0ull;
+            const uint32_t wi = i < e ? w[i] : w0;
+            same &= wi == w0;
+            const unsigned long long x = i < e ? (unsigned long long)wi : 0ull;
             const unsigned long long incl = warp_incl_scan<unsigned long long>(x, lane);
             if (i < e) leaf[i] = ((carry + incl) << 31) | (unsigned long long)(uint32_t)in_src[i];
             carry += __shfl_sync(kFull, incl, 31);
         }
+        same = __all_sync(kFull, same);
         if (lane == 0 && carry > (1ull << 32)) atomicExch(invalid, 1);
         int L = 0;
         for (int64_t t = d; t > 32; t = (t + 31) >> 5) ++L;
         if (lane == 0)
-            vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], (uint32_t)L);
+            vrec[v] = make_uint4((uint32_t)b, (uint32_t)d,
+                                 (uint32_t)tree_off[v] | ((uint32_t)L << 28), same ? w0 : 0u);
         __syncwarp();
         // upper levels, top-down
         unsigned long long *lvl = tree + tree_off[v];
@@ -995,13 +1021,17 @@ __global__ void __launch_bounds__(256) k_lt_index_block(
     for (int j = blockIdx.x; j < nbig; j += gridDim.x) {
         const int64_t v = big[j];
         const int64_t b = in_off[v], e = in_off[v + 1], d = e - b;
+        const uint32_t w0 = w[b];
+        bool same = true;
         unsigned long long carry = 0;
         for (int64_t base = b; base < e; base += 2048) {
             const int64_t i0 = base + (int64_t)tid * 8;
             unsigned long long s[8], run = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                run += i0 + q < e ? (unsigned long long)w[i0 + q] : 0ull;
+                const uint32_t wi = i0 + q < e ? w[i0 + q] : w0;
+                same &= wi == w0;
+                run += i0 + q < e ? (unsigned long long)wi : 0ull;
                 s[q] = run;
             }
             const unsigned long long incl = warp_incl_scan<unsigned long long>(run, lane);
@@ -1022,11 +1052,13 @@ __global__ void __launch_bounds__(256) k_lt_index_block(
             carry += tot;
             __syncthreads();   // wsum is rewritten by the next pass
         }
+        same = __syncthreads_and(same) != 0;
         if (tid == 0 && carry > (1ull << 32)) atomicExch(invalid, 1);
         int L = 0;
         for (int64_t t = d; t > 32; t = (t + 31) >> 5) ++L;
         if (tid == 0)
-            vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], (uint32_t)L);
+            vrec[v] = make_uint4((uint32_t)b, (uint32_t)d,
+                                 (uint32_t)tree_off[v] | ((uint32_t)L << 28), same ? w0 : 0u);
         __syncthreads();   // every leaf of v written by the block is visible to it
         unsigned long long *lvl = tree + tree_off[v];
         for (int l = L; l >= 1; --l) {
@@ -1047,8 +1079,8 @@ __global__ void __launch_bounds__(256) k_lt_index_block(
 // in-edge when none does: {running sum low word, high word, source, e}.
 // Every edge before e has a running sum <= lo_b <= x, so x picks e exactly
 // when x < running sum(e); otherwise the pick lies after e (or there is none).
-__global__ void k_lt_guide(const int64_t *in_off, const unsigned long long *leaf, int64_t n,
-                           int64_t m, uint4 *guide) {
+__global__ void k_lt_guide(const int64_t *in_off, const unsigned long long *leaf,
+                           const uint4 *vrec, int64_t n, int64_t m, uint4 *guide) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
          t += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = n - 1;                  // vertex owning position t
@@ -1057,6 +1089,7 @@ __global__ void k_lt_guide(const int64_t *in_off, const unsigned long long *leaf
             if (in_off[mid] <= t) lo = mid;
             else hi = mid - 1;
         }
+        if (vrec[lo].w != 0u) continue;              // equal weights: no table needed
         const int64_t eb = in_off[lo], d = in_off[lo + 1] - eb, b = t - eb;
         const unsigned long long lob =
             (((unsigned long long)b << 32) + (unsigned long long)d - 1ull) / (unsigned long long)d;
@@ -1410,7 +1443,7 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
     IM_CUDA(cudaMalloc(&x.guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
     if (m > 0) {
         KernelTimer kt(st, "lt_index");
-        k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, x.leaf, n, m, x.guide);
+        k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, x.leaf, x.vrec, n, m, x.guide);
     }
     IM_CUDA(cudaGetLastError());
     int invalid = 0;

@@ -614,3 +614,27 @@ def test_lt_index_flags_weights_above_one(im, hub):
     w[b:e] = np.uint32(1 << 23)               # sum (e - b) 2^23 > 2^32
     G = im.Graph(inputs.Graph(g.n, g.in_off, g.in_src, w))
     assert im.im_graph_info(G.handle)[2] == 0
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_lt_equal_weight_vertices_mixed_with_unequal(im, seed):
+    """Vertices whose in-edges all weigh the same u take the pick from
+    floor(x / u) instead of the cut-point table; here every other vertex has
+    equal weights whose sum d u stays below 2^32 by a random margin (so some
+    draws pick nothing), the rest random weights, over the hub graph's
+    in-degrees (index built by thread, warp and block)."""
+    g = _hub_graph(seed)
+    rng = np.random.default_rng(seed + 100)
+    w = g.w.copy()
+    for v in range(0, g.n, 2):
+        b, e = int(g.in_off[v]), int(g.in_off[v + 1])
+        if e > b:
+            total = rng.uniform(0.3, 1.0) * inputs.U32_MAX
+            w[b:e] = np.uint32(max(1, int(total // (e - b))))
+    g = inputs.Graph(g.n, g.in_off, g.in_src, w)
+    ids = [(0, 9000), (9000, 3001)]
+    G, P = gpu_pool(im, g, im.IM_LT, 77, ids, cap_entries=1 << 24)
+    assert im.im_graph_info(G.handle)[2] == 1
+    ref = oracle_pool(g, 1, 77, ids)
+    assert_pool_equal(im, P, ref)
+    assert_index_equal(P, g, ref)
