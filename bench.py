@@ -546,10 +546,15 @@ def kernel_rooflines(im, cs, per, hbm):
     the algorithmic-byte formulas of each (see the design notes) and the
     kernels' CUDA-event times inside the timed region."""
     T, n, th, k = cs["T"], cs["n"], cs["theta"], cs["k"]
+    passes = max(1, -(-max(n - 1, 0).bit_length() // 8))    # radix passes of <= 8 bits
     alg = {
         "sort_sets_warp": 8 * T + 16 * th,
         "index_hist": 12 * T,
         "index_scatter": 16 * T + 16 * th,
+        # per pass: keys read by the count, keys + values read and written by
+        # the scatter (the first pass reads members only, with set ids from set_off)
+        "index_radix": 16 * T + (passes - 1) * 20 * T + 8 * th,
+        "index_bounds": 4 * T + 8 * n,
         "greedy": 4 * n * k + 4 * cs["s_seed"] + 16 * cs["covered"] + 12 * cs["r_covered"] + th // 8,
         "randgreedi_local": 4 * (cs["rg_eval"] + cs["rg_cover"]) + PARTS * th // 8,
     }

@@ -234,11 +234,17 @@ im_status im_pool_sample_bytes(const im_pool *p, int64_t *bytes);
  *                       many blocks (the smallest of 1, 2, 4, 8 that holds
  *                       it); -1 keeps the bitmaps in global memory (one block
  *                       per bucket).
- *   IM_TUNE_INDEX_REPLICAS  covering-subset build: per-vertex counters and
- *                       cursors replicated 1, 2, 4 (default) or 8 times (a member's
- *                       replica follows its position), spreading the atomics
- *                       on hub vertices; the order of set ids inside an S(v)
- *                       is unspecified in every case.
+ *   IM_TUNE_INDEX_REPLICAS  covering-subset build: 0 (default) a stable radix
+ *                       sort of the (vertex, set id) pairs by vertex, 8 bits a
+ *                       pass, with 12 bytes of pool scratch per member (set ids
+ *                       come out ascending inside every S(v); without the
+ *                       memory, the counting build with 4 replicas runs
+ *                       instead); 1, 2, 4 or 8: a counting build, histogram
+ *                       and scatter through per-vertex counters and cursors
+ *                       replicated that many times (a member's replica
+ *                       follows its position), spreading the atomics on hub
+ *                       vertices.  The order of set ids inside an S(v) is
+ *                       unspecified by the interface in every case.
  *   IM_TUNE_RG_EVALS    RandGreedi local greedy: candidates re-evaluated per
  *                       round, 1, 2 (default), 4 or 8.
  *   IM_TUNE_GREEDY_EVALS  the kernel of IM_GREEDY_PLAIN: 0 (default) runs the
@@ -286,7 +292,7 @@ im_status im_tune_get(int32_t knob, int64_t *value);
  *   out->lt_group, index_replicas, rg_evals, rg_cluster, lt_cache,
  *       greedy_hot: the chosen values (-1 where not tuned);
  *   out->ms[row][i]: the best-of-two time of the i-th value tried (rows: LT
- *       group {1, 8, 16, 32}, replicas {1, 2, 4, 8}, evaluation width
+ *       group {1, 8, 16, 32}, index build {0 (radix), 1, 2, 4, 8}, evaluation width
  *       {1, 2, 4, 8}, bucket stage {0, 1, 2, 4, 8, -1}, LT cache {0, 1, 2},
  *       greedy tau {0, 7, 8, 10}); -1 where not run.
  * Allocates a probe pool (and a small result buffer) and frees them before it

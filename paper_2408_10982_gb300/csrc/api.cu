@@ -102,7 +102,7 @@ std::mutex g_tune_mu;
 // IM_TUNE_LT_GROUP, IM_TUNE_RG_CLUSTER, IM_TUNE_INDEX_REPLICAS, IM_TUNE_RG_EVALS,
 // IM_TUNE_GREEDY_EVALS, IM_TUNE_LT_CACHE, IM_TUNE_GREEDY_HOT
 constexpr int kKnobs = 7;
-int64_t g_tune[kKnobs] = {1, 0, 4, 2, 0, 0, 8};
+int64_t g_tune[kKnobs] = {1, 0, 0, 2, 0, 0, 8};
 }  // namespace
 
 int64_t tune_value(int32_t knob) {
@@ -613,7 +613,7 @@ im_status im_tune_set(int32_t knob, int64_t value) {
                     (knob == IM_TUNE_RG_CLUSTER &&
                      (value == -1 || value == 0 || value == 1 || value == 2 || value == 4 ||
                       value == 8)) ||
-                    (knob == IM_TUNE_INDEX_REPLICAS && (value == 1 || value == 2 || value == 4 ||
+                    (knob == IM_TUNE_INDEX_REPLICAS && (value == 0 || value == 1 || value == 2 || value == 4 ||
                                                         value == 8)) ||
                     (knob == IM_TUNE_RG_EVALS && (value == 1 || value == 2 || value == 4 ||
                                                   value == 8)) ||

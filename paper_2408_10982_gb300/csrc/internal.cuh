@@ -85,38 +85,44 @@ __device__ __forceinline__ void raise_status(int *status, int code) { atomicCAS(
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // Software grid barrier for cooperative launches (all blocks co-resident).
-// Returns false (and raises kDevTimeout) if the other blocks did not arrive
-// within kWaitLimitNs; callers then leave the kernel.
+// The barrier word is one 64-bit arrival counter, zeroed before the launch and
+// never reset: arrival a (counting from 0) belongs to barrier floor(a / nblocks),
+// which every block passes once the counter reaches nblocks times its number
+// plus one.  A block's arrival is one atomic add after a fence (its writes are
+// then visible to every block that passes), its wait a poll of the counter
+// with acquire loads.  Returns false (and raises kDevTimeout) if the other
+// blocks did not arrive within kWaitLimitNs; callers then leave the kernel,
+// and the blocks still waiting give up at their next barrier.
 struct GridBarrier {
-    uint32_t count;
-    uint32_t gen;
+    unsigned long long count;
 };
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, uint32_t nblocks, int *status) {
     __shared__ int ok_flag;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const uint32_t g = ld_acquire_u32(&bar->gen);
         __threadfence();
-        const uint32_t arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            st_release_u32(&bar->gen, g + 1);
-        } else {
-            const uint64_t t0 = global_ns();
-            while (ld_acquire_u32(&bar->gen) == g) {
-                if (global_ns() - t0 > kWaitLimitNs) {
+        const unsigned long long old = atomicAdd(&bar->count, 1ull);
+        const unsigned long long target = (old / nblocks + 1ull) * nblocks;
+        uint64_t t0 = 0;
+        for (uint32_t spin = 0; ld_acquire_u64(&bar->count) < target; ++spin) {
+            if ((spin & 31u) == 31u) {       // the clock is read once per 32 polls
+                const uint64_t t = global_ns();
+                if (t0 == 0) t0 = t;
+                else if (t - t0 > kWaitLimitNs) {
                     raise_status(status, kDevTimeout);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
-        // a block that sees an error raised elsewhere also stops
-        if (ok && *(volatile int *)status == kDevTimeout) ok = 0;
         ok_flag = ok;
     }
     __syncthreads();
@@ -207,7 +213,7 @@ struct im_graph {
     uint32_t *w;         // [m], 16-byte aligned
     // LT search index, built on first LT use: per-vertex records, per-edge
     // leaves (running weight sum << 31 | source) and upper tree levels
-    uint4 *lt_vrec;                  // [n] {edge offset, in-degree, tree offset, 0}
+    uint4 *lt_vrec;                  // [n] {edge offset, in-degree, tree offset | levels << 28, equal in-weight or 0}
     unsigned long long *lt_leaf;     // [m]
     unsigned long long *lt_tree;     // [sum over vertices of the upper-level sizes]
     uint4 *lt_guide;                 // [m] inverse-CDF cut points (see k_lt_guide)
@@ -394,6 +400,11 @@ im_status build_lt_index(im_graph *g, cudaStream_t st);
 
 // index.cu
 im_status build_index(im_pool *p, cudaStream_t st);
+// covering subsets by a stable radix sort (index.cu): scratch bytes, and the build
+size_t radix_index_bytes(int64_t T, int64_t n);
+im_status build_index_radix(const int64_t *set_off, const int32_t *members, int64_t theta,
+                            int64_t T, int64_t n, int64_t *vtx_off, int32_t *set_ids,
+                            int32_t *cnt, void *scratch, cudaStream_t st);
 im_status build_index_raw(const int64_t *set_off, const int32_t *members, int64_t theta, int64_t T,
                           int64_t n, int64_t *vtx_off, int32_t *set_ids, int32_t *cursor,
                           int32_t replicas, void *tmp, cudaStream_t st);

@@ -114,10 +114,10 @@ extern "C" im_status im_autotune(const im_graph *g, im_model model, uint64_t see
             return time_best(st, [&]() { return resample(); }, &err);
         });
     }
-    // counter replicas of the covering-subset build
+    // covering-subset build: radix sort, or counting with 1-8 counter replicas
     {
-        const int64_t v[4] = {1, 2, 4, 8};
-        out->index_replicas = pick(IM_TUNE_INDEX_REPLICAS, v, 4, 1, [&]() {
+        const int64_t v[5] = {0, 1, 2, 4, 8};
+        out->index_replicas = pick(IM_TUNE_INDEX_REPLICAS, v, 5, 1, [&]() {
             return time_best(st, [&]() {
                 im_status r = resample();
                 return r != IM_OK ? r : im_pool_index(p, stream);

@@ -52,19 +52,19 @@ def _no_gpu():
 
 
 def test_tuning_knobs_defaults_values_and_rejections(libpath):
-    """The knob values include/im.h documents: defaults 1, 0, 4, 2, 0, 0, 8; every
+    """The knob values include/im.h documents: defaults 1, 0, 0, 2, 0, 0, 8; every
     allowed value is stored; anything else is IM_ERR_INVALID_ARG and leaves
     the knob unchanged."""
     from paper_2408_10982_gb300 import im
     allowed = {im.IM_TUNE_LT_GROUP: [1, 8, 16, 32],
                im.IM_TUNE_RG_CLUSTER: [-1, 0, 1, 2, 4, 8],
-               im.IM_TUNE_INDEX_REPLICAS: [1, 2, 4, 8],
+               im.IM_TUNE_INDEX_REPLICAS: [0, 1, 2, 4, 8],
                im.IM_TUNE_RG_EVALS: [1, 2, 4, 8],
                im.IM_TUNE_GREEDY_EVALS: [0, 1, 2, 4, 8, 16, 32],
                im.IM_TUNE_LT_CACHE: [0, 1, 2],
                im.IM_TUNE_GREEDY_HOT: [0, 4, 8, 12, 16]}
     defaults = {im.IM_TUNE_LT_GROUP: 1, im.IM_TUNE_RG_CLUSTER: 0,
-                im.IM_TUNE_INDEX_REPLICAS: 4, im.IM_TUNE_RG_EVALS: 2,
+                im.IM_TUNE_INDEX_REPLICAS: 0, im.IM_TUNE_RG_EVALS: 2,
                 im.IM_TUNE_GREEDY_EVALS: 0, im.IM_TUNE_LT_CACHE: 0,
                 im.IM_TUNE_GREEDY_HOT: 8}
     before = {k: im.im_tune_get(k) for k in allowed}

@@ -430,10 +430,12 @@ def test_server_results_equal_alone(im):
         im.im_server_destroy(srv)
 
 
-@pytest.mark.parametrize("replicas", [1, 2, 4, 8])
+@pytest.mark.parametrize("replicas", [0, 1, 2, 4, 8])
 def test_index_replicas_identical(im, replicas):
-    """Replicated counters in the covering-subset build (a tuning knob) give
-    the same covering subsets (as sorted lists) and the same greedy result."""
+    """Every covering-subset build (a tuning knob: radix sort, or counting
+    with 1-8 counter replicas) gives the same covering subsets (as sorted
+    lists; the radix sort's come out ascending, equal to the oracle's as
+    stored) and the same greedy result."""
     old = im.im_tune_get(im.IM_TUNE_INDEX_REPLICAS)
     im.im_tune_set(im.IM_TUNE_INDEX_REPLICAS, replicas)
     try:
@@ -441,6 +443,10 @@ def test_index_replicas_identical(im, replicas):
         G, P = gpu_pool(im, g, im.IM_LT, 42, [(0, 40000)])
         ref = O.sample(O.LT, g, 42, 0, 40000)
         assert_index_equal(P, g, ref)
+        if replicas == 0:
+            vtx_off, set_ids = P.index()
+            rv, rs = O.invert(g.n, ref)
+            assert np.array_equal(vtx_off, rv) and np.array_equal(set_ids, rs)
         c = P.cover(30)
         rc = O.greedy(g.n, ref, O.invert(g.n, ref), 30)
         assert c.seeds.tolist() == rc.seeds.tolist() and c.coverage == rc.coverage
