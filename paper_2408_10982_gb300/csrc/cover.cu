@@ -489,8 +489,13 @@ __device__ void produce(const RGArgs &a, int p, int32_t *key, unsigned long long
                     const int32_t v = vtx[l];
                     const int64_t sb = a.vtx_off[v], se = a.vtx_off[v + 1];
                     int miss = 0;
+                    // L1-cached probes: the bitmap is written only by this
+                    // block (atomics, ordered before these loads by the block
+                    // barriers), and S(v) is scanned in ascending set order
+                    // when the index comes from the radix build, so
+                    // neighbouring ids share cached lines
                     scan_ids<4>(a.set_ids, sb, se - sb, gt, gsz, [&](int32_t i) {
-                        if (i >= 0) miss += !((__ldcg(cov + (i >> 5)) >> (i & 31)) & 1u);
+                        if (i >= 0) miss += !((__ldca(cov + (i >> 5)) >> (i & 31)) & 1u);
                     });
                     miss = warp_sum<int>(miss);
                     if (lane == 0 && miss) atomicAdd(&s_cnt[grp], miss);
