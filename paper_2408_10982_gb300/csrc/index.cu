@@ -33,10 +33,7 @@ __global__ void k_vertex_hist(const int32_t *members, int64_t T, int32_t *cnt, i
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < T;
          base += stride) {
         const int64_t t = base + lane;
-        const int32_t u = t < T ? members[t] : -1 - lane;   // distinct dummies
-        const unsigned peers = __match_any_sync(kFull, u);
-        if (u >= 0 && lane == __ffs(peers) - 1)
-            atomicAdd(&cnt[replica_of(t, R) * n + u], __popc(peers));
+        if (t < T) red_add_s32(&cnt[replica_of(t, R) * n + members[t]], 1);
     }
 }
 
@@ -71,7 +68,7 @@ __global__ void k_scatter(const int64_t *set_off, const int32_t *members, int64_
         const int64_t incl = warp_incl_scan<int64_t>(len, lane);
         const int64_t total = __shfl_sync(kFull, incl, 31);
         const int64_t first = set_off[i0];
-        constexpr int U = 4;
+        constexpr int U = 8;
         for (int64_t base = 0; base < total; base += 32 * U) {
             int32_t sid[U], u[U];
             int64_t t[U], pos[U];
@@ -137,12 +134,7 @@ __global__ void __launch_bounds__(kRxThreads) k_rx_count(const int32_t *keys, in
 #pragma unroll 4
         for (int j = 0; j < kRxItems; ++j) {
             const int64_t t = rx_pos(tile, w, j, lane);
-            const bool ok = t < T;
-            const uint32_t d =
-                ok ? ((uint32_t)__ldg(keys + t) >> shift) & mask : (uint32_t)(kRxMaxBins + lane);
-            const unsigned peers = __match_any_sync(kFull, d);
-            if (ok && lane == __ffs(peers) - 1) h[w][d] += __popc(peers);
-            __syncwarp();
+            if (t < T) atomicAdd(&h[w][((uint32_t)__ldg(keys + t) >> shift) & mask], 1);
         }
         __syncthreads();
         for (int d = threadIdx.x; d < bins; d += kRxThreads) {

@@ -644,3 +644,30 @@ def test_lt_equal_weight_vertices_mixed_with_unequal(im, seed):
     ref = oracle_pool(g, 1, 77, ids)
     assert_pool_equal(im, P, ref)
     assert_index_equal(P, g, ref)
+
+
+def test_ic_giant_sets_through_hubs(im):
+    """Giant sets (second pass, one block per set) that pass through hubs of
+    4,096 to 20,011 in-edges with unaligned first edges, reached from every
+    root (every vertex has in-edges from three hubs)."""
+    rng = np.random.default_rng(12)
+    n = 30000
+    hub_deg = [4096, 4097, 5001, 9000, 20011, 4099 * 4 + 3]
+    src, dst = [], []
+    for h, d in enumerate(hub_deg):
+        s = rng.choice(np.arange(len(hub_deg), n), size=d, replace=False)
+        src += s.tolist()
+        dst += [h] * d
+    for v in range(len(hub_deg), n):
+        hs = rng.choice(len(hub_deg), size=3, replace=False)
+        rs = rng.integers(len(hub_deg), n, size=2)
+        for u in set(hs.tolist() + rs.tolist()) - {v}:
+            src.append(u)
+            dst.append(v)
+    in_off, in_src = inputs.in_csr(n, np.array(src), np.array(dst))
+    w = np.full(in_src.size, np.uint32(int(0.9 * inputs.U32_MAX)))
+    g = inputs.Graph(n, in_off, in_src, w)
+    G, P = gpu_pool(im, g, im.IM_IC, 31, [(0, 150), (150, 61)], cap_entries=211 * n)
+    ref = oracle_pool(g, O.IC, 31, [(0, 150), (150, 61)])
+    assert np.diff(ref.set_off).max() > 16384
+    assert_pool_equal(im, P, ref)
