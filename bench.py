@@ -647,6 +647,13 @@ def bench_batched(im, torch):
     out = im.im_solve_batch(batch, qlist, 100, with_partitions=True)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
+    # the same call again with per-kernel events, for the phase breakdown
+    im.im_profile_reset()
+    im.im_profile_enable(True)
+    im.im_solve_batch(batch, qlist, 100)
+    torch.cuda.synchronize()
+    im.im_profile_enable(False)
+    phases = {k: round(v[1], 2) for k, v in sorted(im.im_profile_read().items()) if v[1] >= 1.0}
     im.im_batch_destroy(batch)
     parts = [o[4] for o in out]
     one = OneQuery(im, G)
@@ -672,7 +679,8 @@ def bench_batched(im, torch):
             "randgreedi_queries": sum(1 for p in parts if p), "partition_counts_chosen": chosen,
             "q_per_s": round(len(specs) / t_batch, 2), "ms": round(1000 * t_batch, 2),
             "plain_q_per_s": round(len(specs) / t_plain, 2), "plain_ms": round(1000 * t_plain, 2),
-            "speedup_vs_plain": round(t_plain / t_batch, 3), "bit_exact_vs_plain": bool(same)}
+            "speedup_vs_plain": round(t_plain / t_batch, 3), "bit_exact_vs_plain": bool(same),
+            "phase_ms": phases}
 
 
 def bench_served(im, torch, orkut: bool):

@@ -685,6 +685,7 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
 constexpr int kLT1Threads = 256;
 constexpr int kBloomWords = 32;              // 1024 bits per walk
 constexpr int64_t kQueueCapLT1 = 512;
+constexpr unsigned kLT1Chunk = 64;           // sample indices a warp takes at once
 
 __device__ __forceinline__ uint32_t bloom_h1(uint32_t u) { return (u * 0x9E3779B1u) >> 22; }
 __device__ __forceinline__ uint32_t bloom_h2(uint32_t u) {
@@ -728,7 +729,7 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first() {
 // at every step) are kept in L2 ahead of other lines (evict_last); 2 as 1, and
 // the cut points (m x 16 B, mostly single-use) leave L2 first (evict_first).
 template <int CP>
-__global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
+__global__ void __launch_bounds__(kLT1Threads, 5) k_sample_lt1(SampleArgs a) {
     extern __shared__ uint32_t bloom[];          // [kBloomWords][kLT1Threads]
     const uint64_t pol_v = CP >= 1 ? l2_policy_evict_last() : 0ull;
     const uint64_t pol_c = CP >= 2 ? l2_policy_evict_first() : 0ull;
@@ -745,17 +746,29 @@ __global__ void __launch_bounds__(kLT1Threads) k_sample_lt1(SampleArgs a) {
     int32_t len = 0;
     unsigned long long sexam = 0, exam = 0, abytes = 0;
     uint32_t sbytes = 0;
+    // the warp's current chunk of sample indices [wnext, wend), taken from the
+    // global counter kLT1Chunk at a time (warp-uniform)
+    unsigned long long wnext = 0, wend = 0;
     for (;;) {
-        // ---- lanes without a walk take the next samples (one atomic per warp)
+        // ---- lanes without a walk take the next samples of the warp's chunk
         const bool want = !active && !exhausted;
         const unsigned need = __ballot_sync(kFull, want);
         if (need) {
-            const int leader = __ffs(need) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(need));
-            base = __shfl_sync(kFull, base, leader);
+            const unsigned nneed = (unsigned)__popc(need);
+            const unsigned rank = __popc(need & ((1u << lane) - 1u));
+            const unsigned long long avail = wend - wnext;
+            unsigned long long jw = wnext + rank;
+            if (avail < nneed) {                     // the rest of this chunk, then a new one
+                unsigned long long nb = 0;
+                if (lane == 0) nb = atomicAdd(a.work, (unsigned long long)kLT1Chunk);
+                nb = __shfl_sync(kFull, nb, 0);
+                if (rank >= avail) jw = nb + (rank - avail);
+                wnext = nb + (nneed - avail);
+                wend = nb + kLT1Chunk;
+            } else {
+                wnext += nneed;
+            }
             if (want) {
-                const unsigned long long jw = base + __popc(need & ((1u << lane) - 1u));
                 if (jw < (unsigned long long)a.count) {
                     j = a.list ? a.list[jw] : (int64_t)jw;
                     const int qi = find_query(a, j);
