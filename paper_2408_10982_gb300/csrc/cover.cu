@@ -150,6 +150,10 @@ struct GreedyArgs {
 };
 
 constexpr int kHubRep = 32;             // partial counts of a hub (one per set id mod 32)
+// Entries of S(v*) a warp claims at a time: a chunk's newly covered sets can
+// hold hundreds of members each, so small chunks spread the decrements over
+// more warps (the step waits for the slowest one).
+constexpr int kGreedyChunk = 16;
 constexpr int kHubCap = 4096;           // hub rows at most
 constexpr int kHubShift = 6;            // hubs: |S(v)| >= max |S(v)| / 64
 
@@ -169,7 +173,7 @@ constexpr int kHubShift = 6;            // hubs: |S(v)| >= max |S(v)| / 64
 // keeping |S(v)| as a stale bound -- which skips most decrements (low-degree
 // vertices are most members).  Once the best gain falls below tau, one pass
 // makes the frozen gains exact and every step reads all.
-// Warps take 32-entry chunks of S(v*) from a per-step counter.  Every wait is
+// Warps take kGreedyChunk-entry chunks of S(v*) from a per-step counter.  Every wait is
 // bounded (grid_sync).
 __global__ void __launch_bounds__(kGreedyThreads, 2) k_greedy(GreedyArgs a) {
     __shared__ unsigned long long shm[33];
@@ -296,16 +300,16 @@ __global__ void __launch_bounds__(kGreedyThreads, 2) k_greedy(GreedyArgs a) {
         // closing barrier)
         unsigned long long *work = a.work ? a.work + (j & 1) : nullptr;
         if (work && blockIdx.x == 0 && threadIdx.x == 0) a.work[(j + 1) & 1] = 0ull;
-        for (int64_t base = sb + gwarp * 32;;) {
+        for (int64_t base = sb + gwarp * kGreedyChunk;;) {
             if (work) {
                 unsigned long long c = 0;
-                if (lane == 0) c = atomicAdd(work, 32ull);
+                if (lane == 0) c = atomicAdd(work, (unsigned long long)kGreedyChunk);
                 base = sb + (int64_t)__shfl_sync(kFull, c, 0);
             }
             if (base >= se) break;
             const int64_t t = base + lane;
             int32_t i = -1;
-            if (t < se) i = a.set_ids[t];
+            if (lane < kGreedyChunk && t < se) i = a.set_ids[t];
             const bool fresh = warp_bitmap_set(a.covered, i >= 0 ? i - a.sshift : -1, lane);
             if (__any_sync(kFull, fresh)) {
                 // decrement the gains of every member of the lane's newly
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(kGreedyThreads, 2) k_greedy(GreedyArgs a) {
                     }
                 }
             }
-            if (!work) base += nwarps * 32;
+            if (!work) base += nwarps * kGreedyChunk;
         }
         if (!grid_sync(a.bar, nb, a.status)) return;
         ++j;
