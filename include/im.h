@@ -507,6 +507,12 @@ typedef struct {
     int32_t workers;          /* batches in flight at once, 1..16 */
     int32_t max_batch;        /* requests per batch, >= 1 */
     int64_t mem_budget;       /* device bytes the in-flight batches may use */
+    int64_t heavy_members;    /* 0: off.  > 0 (needs workers >= 2): a request whose estimated
+                                 RRR members (theta x members per set seen so far on its graph
+                                 and model, 64 before any) reach this runs on worker 0 only;
+                                 the other workers take the remaining requests in arrival
+                                 order past it (a heavy lane, so long queries do not hold up
+                                 short ones) */
 } im_server_opts;
 
 typedef struct im_server im_server;

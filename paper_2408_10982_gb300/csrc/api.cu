@@ -191,6 +191,21 @@ im_status dev_alloc(void **p, size_t bytes) {
     return IM_OK;
 }
 
+im_status raise_dyn_smem(const void *func, size_t bytes) {
+    constexpr size_t kDefault = 48 * 1024;   // the limit without opting in
+    if (bytes <= kDefault) return IM_OK;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    int dev = 0;
+    IM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limit[{dev, func}];
+    if (bytes <= cur) return IM_OK;
+    IM_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return IM_OK;
+}
+
 void dev_free(void *p) {
     if (!p) return;
     DevHeap *h = nullptr;

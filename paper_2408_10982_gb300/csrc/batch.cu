@@ -567,8 +567,7 @@ im_status im_solve_batch(im_batch *b, const im_query *qs, int32_t nq, int32_t km
             set_error("im_solve_batch: a query graph is too large for the batched greedy");
             return IM_ERR_UNSUPPORTED;
         }
-        IM_CUDA(cudaFuncSetAttribute(k_batch_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+        IM_TRY(raise_dyn_smem((const void *)k_batch_greedy, smem));
         if (n_grid < ng) {
             KernelTimer kt(st, "batch_greedy");
             k_batch_greedy<<<(unsigned)std::min<int64_t>(nq, (int64_t)num_sms() * 2), kBGThreads, smem,

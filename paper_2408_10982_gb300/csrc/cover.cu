@@ -1461,8 +1461,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
     a.slot_len = use_masks ? (int64_t *)(Bs + o_sl) : nullptr;
     if (use_masks) IM_CUDA(cudaMemsetAsync(Bs + o_bar, 0, sizeof(GridBarrier), st));
 
-    IM_CUDA(cudaFuncSetAttribute(k_randgreedi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)prod_smem));
+    IM_TRY(raise_dyn_smem((const void *)k_randgreedi, prod_smem));
     int per_sm = 0;
     IM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_randgreedi, kRGThreads,
                                                           prod_smem));
@@ -1480,8 +1479,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
                                             prod_smem, st));
     } else {
         // producers alone, then consumers alone (the stream is complete by then)
-        IM_CUDA(cudaFuncSetAttribute(k_rg_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)prod_smem));
+        IM_TRY(raise_dyn_smem((const void *)k_rg_local, prod_smem));
         int per_l = 0;
         IM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, k_rg_local, kProdThreads,
                                                               prod_smem));
@@ -1534,8 +1532,7 @@ im_status randgreedi(im_pool *p, int32_t k, const im_cover_opts *o, int32_t *d_s
         } else if (CS <= 8) {
             unsigned *counter = (unsigned *)(Bs + o_l) + 2;
             IM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
-            IM_CUDA(cudaFuncSetAttribute(k_rg_stream_cluster,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+            IM_TRY(raise_dyn_smem((const void *)k_rg_stream_cluster, csmem));
             const int nclusters = std::max(1, std::min<int>(B, num_sms() / CS));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(nclusters * CS);

@@ -438,10 +438,8 @@ im_status build_index_radix(const int64_t *set_off, const int32_t *members, int6
         const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 2);
         const size_t smem = (size_t)2 * kRxTile * 4;
         // the scatter's 64 KB of dynamic shared memory (a per-device attribute)
-        IM_CUDA(cudaFuncSetAttribute(k_rx_scatter<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        IM_CUDA(cudaFuncSetAttribute(k_rx_scatter<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        IM_TRY(raise_dyn_smem((const void *)k_rx_scatter<true>, smem));
+        IM_TRY(raise_dyn_smem((const void *)k_rx_scatter<false>, smem));
         const int32_t *kin = members, *vin = nullptr;
         for (int ps = 0; ps < passes; ++ps) {
             const int shift = ps * width;

@@ -400,6 +400,13 @@ im_status build_lt_index(im_graph *g, cudaStream_t st);
 
 // index.cu
 im_status build_index(im_pool *p, cudaStream_t st);
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`, never lowering it (api.cu).  Launches of one kernel from
+// several host threads with different sizes (serving workers) then all stay
+// within the limit; setting the attribute to each launch's own size would let
+// one thread lower it under another's launch.
+im_status raise_dyn_smem(const void *func, size_t bytes);
+
 // covering subsets by a stable radix sort (index.cu): scratch bytes, and the build
 size_t radix_index_bytes(int64_t T, int64_t n);
 im_status build_index_radix(const int64_t *set_off, const int32_t *members, int64_t theta,

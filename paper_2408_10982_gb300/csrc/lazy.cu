@@ -546,8 +546,7 @@ im_status greedy_lazy_launch(int64_t n, int64_t theta, const int64_t *vtx_off,
                              const int32_t *cand_seeds, const int32_t *cand_n, int32_t cand_parts,
                              int32_t cand_take, int32_t cand_stride) {
     const size_t smem = lazy_greedy_smem();
-    IM_CUDA(cudaFuncSetAttribute((const void *)k_greedy_lazy,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    IM_TRY(raise_dyn_smem((const void *)k_greedy_lazy, smem));
     int per_sm = 0;
     IM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_lazy, kLzThreads, smem));
     if (per_sm < 1) {

@@ -1217,8 +1217,71 @@ __device__ __forceinline__ void bitonic_smem(Key *buf, int P, int tid, int nthre
     }
 }
 
+// Bitonic sort of N keys held by one thread (N a power of two, fully unrolled).
+template <typename Key, int N>
+__device__ __forceinline__ void thread_bitonic(Key (&v)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool asc = (i & k) == 0;
+                    const Key x = v[i], y = v[l];
+                    const bool sw = asc ? (y < x) : (x < y);
+                    v[i] = sw ? y : x;
+                    v[l] = sw ? x : y;
+                }
+            }
+        }
+    }
+}
+
+// One segment sorted by the whole warp (len > kLaneSort): copied from the
+// stage and sorted in registers, or in the warp's shared buffer, or listed in
+// `big` for k_sort_block / k_sort_giant.
+template <typename Key>
+__device__ __forceinline__ void warp_sort_segment(Key *out, const Key *src, int64_t len,
+                                                  bool from_stage, int64_t i, Key *buf,
+                                                  int64_t *big, unsigned long long *nbig,
+                                                  int lane) {
+    constexpr int kCapW = kWarpSortBytes / (int)sizeof(Key);
+    if (len <= 32) {
+        Key v = lane < len ? src[lane] : key_max<Key>();
+        v = warp_bitonic32<Key>(v, lane);
+        if (lane < len) out[lane] = v;
+    } else if (len <= 64) {
+        warp_sort_copy<Key, 2>(out, src, len, lane);
+    } else if (len <= 128) {
+        warp_sort_copy<Key, 4>(out, src, len, lane);
+    } else if (len <= 256) {
+        warp_sort_copy<Key, 8>(out, src, len, lane);
+    } else if (len <= 512 && sizeof(Key) == 4) {
+        warp_sort_copy<Key, 16>(out, src, len, lane);
+    } else if (len <= kCapW) {
+        int P = 64;
+        while (P < len) P <<= 1;
+        for (int t = lane; t < P; t += 32) buf[t] = t < len ? src[t] : key_max<Key>();
+        __syncwarp();
+        bitonic_smem<Key>(buf, P, lane, 32, false);
+        for (int t = lane; t < len; t += 32) out[t] = buf[t];
+    } else {
+        if (from_stage)
+            for (int64_t t = lane; t < len; t += 32) out[t] = src[t];
+        if (lane == 0) big[atomicAdd(nbig, 1ull)] = i;
+    }
+    __syncwarp();
+}
+
 // Copies stage segments into place (when `stage` is non-null) and sorts every
-// segment of up to 4 KB of keys with one warp; longer ones go to `big`.
+// segment of up to 4 KB of keys; longer ones go to `big`.  A warp takes 32
+// consecutive segments at once (their offsets in one coalesced load each):
+// segments of at most kLaneSort keys -- most RRR sets -- are sorted by their
+// own lane in registers, the others by the whole warp one after another.
+constexpr int kLaneSort = 16;
+
 template <typename Key>
 __global__ void __launch_bounds__(256) k_sort_small(Key *dst, const int64_t *seg_off, int64_t nseg,
                                                     const Key *stage, const int64_t *stage_off,
@@ -1227,39 +1290,39 @@ __global__ void __launch_bounds__(256) k_sort_small(Key *dst, const int64_t *seg
     __shared__ Key sbuf[8][kCapW];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t nw = (int64_t)gridDim.x * 8;
-    for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < nseg; i += nw) {
-        const int64_t o = seg_off[i];
-        const int64_t len = seg_off[i + 1] - o;
-        const Key *src = stage ? stage + stage_off[i] : dst + o;
-        Key *out = dst + o;
-        if (len <= 1) {
-            if (len == 1 && stage && lane == 0) out[0] = src[0];
-        } else if (len <= 32) {
-            Key v = lane < len ? src[lane] : key_max<Key>();
-            v = warp_bitonic32<Key>(v, lane);
-            if (lane < len) out[lane] = v;
-        } else if (len <= 64) {
-            warp_sort_copy<Key, 2>(out, src, len, lane);
-        } else if (len <= 128) {
-            warp_sort_copy<Key, 4>(out, src, len, lane);
-        } else if (len <= 256) {
-            warp_sort_copy<Key, 8>(out, src, len, lane);
-        } else if (len <= 512 && sizeof(Key) == 4) {
-            warp_sort_copy<Key, 16>(out, src, len, lane);
-        } else if (len <= kCapW) {
-            int P = 64;
-            while (P < len) P <<= 1;
-            Key *buf = sbuf[wib];
-            for (int t = lane; t < P; t += 32) buf[t] = t < len ? src[t] : key_max<Key>();
-            __syncwarp();
-            bitonic_smem<Key>(buf, P, lane, 32, false);
-            for (int t = lane; t < len; t += 32) out[t] = buf[t];
-        } else {
-            if (stage)
-                for (int64_t t = lane; t < len; t += 32) out[t] = src[t];
-            if (lane == 0) big[atomicAdd(nbig, 1ull)] = i;
+    for (int64_t i0 = ((int64_t)blockIdx.x * 8 + wib) * 32; i0 < nseg; i0 += nw * 32) {
+        const int64_t i = i0 + lane;
+        int64_t o = 0, len = 0, so = 0;
+        if (i < nseg) {
+            o = seg_off[i];
+            len = seg_off[i + 1] - o;
+            so = stage ? stage_off[i] : o;
         }
-        __syncwarp();
+        const Key *src = stage ? stage + so : dst + o;
+        Key *out = dst + o;
+        // ---- short segments: one lane each
+        if (len == 1) {
+            if (stage) out[0] = src[0];
+        } else if (len > 1 && len <= kLaneSort) {
+            Key v[kLaneSort];
+#pragma unroll
+            for (int r = 0; r < kLaneSort; ++r) v[r] = r < len ? src[r] : key_max<Key>();
+            thread_bitonic<Key, kLaneSort>(v);
+#pragma unroll
+            for (int r = 0; r < kLaneSort; ++r)
+                if (r < len) out[r] = v[r];
+        }
+        // ---- the others: the whole warp, one segment at a time
+        unsigned todo = __ballot_sync(kFull, len > kLaneSort);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t ol = __shfl_sync(kFull, o, l);
+            const int64_t ll = __shfl_sync(kFull, len, l);
+            const int64_t sl = __shfl_sync(kFull, so, l);
+            warp_sort_segment<Key>(dst + ol, stage ? stage + sl : dst + ol, ll, stage != nullptr,
+                                   i0 + l, sbuf[wib], big, nbig, lane);
+        }
     }
 }
 
@@ -1371,8 +1434,7 @@ im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, c
     }
     constexpr int kCap = kBlockSortCap * 4 / (int)sizeof(Key);
     const size_t smem = (size_t)kCap * sizeof(Key);
-    IM_CUDA(cudaFuncSetAttribute(k_sort_block<Key, kCap>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    IM_TRY(raise_dyn_smem((const void *)k_sort_block<Key, kCap>, smem));
     {
         KernelTimer kt(st, block_name);
         k_sort_block<Key, kCap><<<num_sms(), 1024, smem, st>>>(keys, seg_off, big, ctr,
@@ -1519,8 +1581,7 @@ im_status run_sampling(const SamplingJob &job, const std::function<im_status(siz
                             : lt1    ? (size_t)kBloomWords * kLT1Threads * 4
                                      : 0;
     if (dyn_smem > 48 * 1024)
-        IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)dyn_smem));
+        IM_TRY(raise_dyn_smem(kern, dyn_smem));
     int blocks = blocks_for(kern, threads, dyn_smem);
     // global visited bitmaps are n bits per warp: keep them within ~2 GB
     if (model == IM_IC && !smem_vis) {

@@ -7,14 +7,18 @@
 // estimated from theta and the members per set seen so far on its graph and
 // model), solve them with im_solve_batch, and publish the results.  Requests
 // that arrive while batches are on the GPU wait for the next free worker;
-// with several workers, batches overlap on the device.  A result does not
-// depend on the batch it ran in.
+// with several workers, batches overlap on the device.  With a heavy lane
+// (opts.heavy_members > 0), requests whose estimated RRR members reach that
+// bound run on worker 0 only, and the other workers take the rest in arrival
+// order past them, so a few long queries do not hold up the short ones
+// queued behind them.  A result does not depend on the batch it ran in.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <new>
 #include <thread>
 #include <unordered_map>
@@ -30,8 +34,10 @@ struct Request {
     im_query q;
     Clock::time_point submitted, finished;
     int64_t footprint = 0;
+    bool heavy = false;       // runs on worker 0 only (the heavy lane)
     bool done = false;
     im_status status = IM_OK;
+    std::string error;        // the failing batch's message (set in the worker's thread)
     std::vector<int32_t> seeds;
     int64_t coverage = 0;
     int64_t entries = 0;
@@ -73,8 +79,16 @@ int64_t footprint(im_server *s, const im_query &q) {
            q.graph->n * 24 + rg + 4096;
 }
 
-void worker_main(im_server *s) {
+// Estimated RRR members of a request (theta x members per set seen so far).
+double est_members(im_server *s, const im_query &q) {
+    auto it = s->per_set.find({q.graph, q.model});
+    const double per = it != s->per_set.end() ? it->second : 64.0;
+    return (double)q.theta * per;
+}
+
+void worker_main(im_server *s, int32_t wid) {
     cudaSetDevice(s->device);
+    const bool any = wid == 0 || s->opts.heavy_members <= 0;   // may this worker run heavy ones
     cudaStream_t st = nullptr;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     im_batch *b = nullptr;
@@ -83,25 +97,37 @@ void worker_main(im_server *s) {
     std::vector<im_query> qs;
     for (;;) {
         std::unique_lock<std::mutex> lk(s->mu);
+        // the first queued request this worker may run
+        auto first_mine = [&]() {
+            for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+                if (any || !s->reqs[*it].heavy) return it;
+            return s->queue.end();
+        };
         s->cv_work.wait(lk, [&] {
-            if (s->stop && s->queue.empty()) return true;
-            if (s->queue.empty()) return false;
-            const Request &r = s->reqs[s->queue.front()];
+            const auto it = first_mine();
+            if (it == s->queue.end()) return s->stop;
+            const Request &r = s->reqs[*it];
             return s->in_flight == 0 || s->mem_in_use + r.footprint <= s->opts.mem_budget;
         });
-        if (s->queue.empty()) break;   // stop requested and nothing left
-        // admit in arrival order while the batch and the memory budget allow
+        // stop requested and nothing left for this worker (worker 0 drains the heavy lane)
+        if (first_mine() == s->queue.end()) break;
+        // admit in arrival order (past the heavy lane's requests on the other
+        // workers) while the batch and the memory budget allow
         ids.clear();
         qs.clear();
         int64_t mem = 0;
-        while (!s->queue.empty() && (int32_t)ids.size() < s->opts.max_batch) {
-            const uint64_t t = s->queue.front();
-            Request &r = s->reqs[t];
+        for (auto it = s->queue.begin();
+             it != s->queue.end() && (int32_t)ids.size() < s->opts.max_batch;) {
+            Request &r = s->reqs[*it];
+            if (!any && r.heavy) {
+                ++it;
+                continue;
+            }
             if (!ids.empty() && s->mem_in_use + mem + r.footprint > s->opts.mem_budget) break;
             mem += r.footprint;
-            ids.push_back(t);
+            ids.push_back(*it);
             qs.push_back(r.q);
-            s->queue.pop_front();
+            it = s->queue.erase(it);
         }
         s->mem_in_use += mem;
         s->in_flight++;
@@ -113,6 +139,10 @@ void worker_main(im_server *s) {
         std::vector<im_result> res(qs.size());
         const im_status st_batch =
             im_solve_batch(b, qs.data(), (int32_t)qs.size(), kmax, seeds.data(), nullptr, res.data(), st);
+        const std::string err = st_batch == IM_OK ? std::string() : std::string(im_last_error());
+        // a batch that failed part way may still have work queued on the stream:
+        // let it finish before the arena is reused or the worker leaves
+        if (st_batch != IM_OK) cudaStreamSynchronize(st);
         const auto now = Clock::now();
 
         lk.lock();
@@ -121,6 +151,7 @@ void worker_main(im_server *s) {
             r.done = true;
             r.finished = now;
             r.status = st_batch;
+            r.error = err;
             if (st_batch == IM_OK) {
                 r.seeds.assign(seeds.begin() + (int64_t)i * kmax,
                                seeds.begin() + (int64_t)i * kmax + res[i].num_seeds);
@@ -150,6 +181,7 @@ im_status take_result(im_server *s, uint64_t ticket, int32_t *seeds, int32_t *nu
     auto it = s->reqs.find(ticket);
     Request &r = it->second;
     const im_status st = r.status;
+    if (st != IM_OK) im::set_error("im_server: the request's batch failed: " + r.error);
     if (st == IM_OK) {
         if (seeds && !r.seeds.empty()) std::memcpy(seeds, r.seeds.data(), r.seeds.size() * 4);
         if (num_seeds) *num_seeds = (int32_t)r.seeds.size();
@@ -170,7 +202,8 @@ extern "C" {
 
 im_status im_server_create(const im_server_opts *opts, im_server **out) {
     if (!opts || !out || opts->workers < 1 || opts->workers > 16 || opts->max_batch < 1 ||
-        opts->mem_budget <= 0) {
+        opts->mem_budget <= 0 || opts->heavy_members < 0 ||
+        (opts->heavy_members > 0 && opts->workers < 2)) {
         set_error("im_server_create: bad options");
         return IM_ERR_INVALID_ARG;
     }
@@ -178,7 +211,7 @@ im_status im_server_create(const im_server_opts *opts, im_server **out) {
     if (!s) return IM_ERR_OOM;
     s->opts = *opts;
     cudaGetDevice(&s->device);
-    for (int32_t w = 0; w < opts->workers; ++w) s->workers.emplace_back(worker_main, s);
+    for (int32_t w = 0; w < opts->workers; ++w) s->workers.emplace_back(worker_main, s, w);
     *out = s;
     return IM_OK;
 }
@@ -209,10 +242,12 @@ im_status im_server_submit(im_server *s, const im_query *q, uint64_t *ticket) {
         r.q = *q;
         r.submitted = Clock::now();
         r.footprint = footprint(s, *q);
+        r.heavy = s->opts.heavy_members > 0 &&
+                  est_members(s, *q) >= (double)s->opts.heavy_members;
         s->queue.push_back(t);
         *ticket = t;
     }
-    s->cv_work.notify_one();
+    s->cv_work.notify_all();   // the right worker for this request may not be the first woken
     return IM_OK;
 }
 

@@ -388,12 +388,13 @@ def im_autotune(g, model: int, seed: int, theta: int, k: int, rg_opts: CoverOpts
 class ServerOpts(ctypes.Structure):
     """im_server_opts (see include/im.h)."""
     _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("mem_budget", ctypes.c_int64)]
+                ("mem_budget", ctypes.c_int64), ("heavy_members", ctypes.c_int64)]
 
 
-def im_server_create(workers: int = 2, max_batch: int = 256, mem_budget: int = 64 << 30):
+def im_server_create(workers: int = 2, max_batch: int = 256, mem_budget: int = 64 << 30,
+                     heavy_members: int = 0):
     h = ctypes.c_void_p()
-    o = ServerOpts(workers, max_batch, mem_budget)
+    o = ServerOpts(workers, max_batch, mem_budget, heavy_members)
     _check(lib().im_server_create(ctypes.byref(o), ctypes.byref(h)), "im_server_create")
     return h
 

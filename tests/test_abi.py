@@ -112,6 +112,12 @@ def test_invalid_arguments_rejected_before_any_device_work(libpath):
     with pytest.raises(im.ImError) as e:
         im.im_pool_create(None, 10, 10)
     assert e.value.status == im.IM_ERR_INVALID_ARG
+    # server options: a heavy lane needs a second worker; bounds are positive
+    for kw in (dict(workers=1, heavy_members=1000), dict(workers=2, heavy_members=-1),
+               dict(workers=0), dict(workers=17), dict(max_batch=0), dict(mem_budget=0)):
+        with pytest.raises(im.ImError) as e:
+            im.im_server_create(**kw)
+        assert e.value.status == im.IM_ERR_INVALID_ARG
 
 
 @pytest.mark.skipif(not _no_gpu(), reason="checks the answer on a machine without a GPU")

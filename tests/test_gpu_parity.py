@@ -395,14 +395,18 @@ def test_solve_batch_randgreedi_queries(im):
         gh.close()
 
 
-def test_server_results_equal_alone(im):
+@pytest.mark.parametrize("heavy", [0, 60000])
+def test_server_results_equal_alone(im, heavy):
     """Continuous batching: requests submitted back to back land in shared
-    batches, and every result equals the oracle's (= the query alone)."""
+    batches, and every result equals the oracle's (= the query alone); with a
+    heavy lane (the larger requests on worker 0 only, the rest past them)
+    as well."""
     import time
     graphs = [inputs.rmat_graph(1 << 12, 1 << 16, 5, "ic0.1"),
               inputs.rmat_graph(1 << 13, 1 << 17, 6, "lt")]
     G = [im.Graph(g) for g in graphs]
-    srv = im.im_server_create(workers=2, max_batch=16, mem_budget=8 << 30)
+    srv = im.im_server_create(workers=3 if heavy else 2, max_batch=16, mem_budget=8 << 30,
+                              heavy_members=heavy)
     rng = np.random.default_rng(3)
     reqs = []
     try:
