@@ -509,7 +509,10 @@ typedef struct {
     int64_t mem_budget;       /* device bytes the in-flight batches may use */
     int64_t heavy_members;    /* 0: off.  > 0 (needs workers >= 2): a request whose estimated
                                  RRR members (theta x members per set seen so far on its graph
-                                 and model, 64 before any) reach this runs on worker 0 only;
+                                 and model, 64 before any) reach this runs on worker 0 only,
+                                 by itself through the single-query path (im_sample_rrr into
+                                 a pool the worker keeps, then im_max_k_cover; a RandGreedi
+                                 request with partitions = 0 still goes through a batch);
                                  the other workers take the remaining requests in arrival
                                  order past it (a heavy lane, so long queries do not hold up
                                  short ones) */

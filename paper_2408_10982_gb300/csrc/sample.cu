@@ -1275,32 +1275,33 @@ __device__ __forceinline__ void warp_sort_segment(Key *out, const Key *src, int6
     __syncwarp();
 }
 
-// Copies stage segments into place (when `stage` is non-null) and sorts every
-// segment of up to 4 KB of keys; longer ones go to `big`.  A warp takes 32
-// consecutive segments at once (their offsets in one coalesced load each):
-// segments of at most kLaneSort keys -- most RRR sets -- are sorted by their
-// own lane in registers, the others by the whole warp one after another.
+// Copies stage segments into place (when `stage` is non-null) and sorts the
+// short ones.  A warp takes 32 consecutive segments at once (their offsets in
+// one coalesced load each): segments of at most kLaneSort keys -- most RRR
+// sets -- are sorted by their own lane in registers; the longer ones are
+// listed in `mid` for k_sort_mid, one warp each.
 constexpr int kLaneSort = 16;
 
 template <typename Key>
 __global__ void __launch_bounds__(256) k_sort_small(Key *dst, const int64_t *seg_off, int64_t nseg,
                                                     const Key *stage, const int64_t *stage_off,
-                                                    int64_t *big, unsigned long long *nbig) {
+                                                    int64_t *mid, unsigned long long *nmid,
+                                                    bool inline_long, int64_t *big,
+                                                    unsigned long long *nbig) {
     constexpr int kCapW = kWarpSortBytes / (int)sizeof(Key);
     __shared__ Key sbuf[8][kCapW];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t nw = (int64_t)gridDim.x * 8;
     for (int64_t i0 = ((int64_t)blockIdx.x * 8 + wib) * 32; i0 < nseg; i0 += nw * 32) {
         const int64_t i = i0 + lane;
-        int64_t o = 0, len = 0, so = 0;
+        int64_t o = 0, len = 0;
+        const Key *src = nullptr;
         if (i < nseg) {
             o = seg_off[i];
             len = seg_off[i + 1] - o;
-            so = stage ? stage_off[i] : o;
+            src = stage ? stage + stage_off[i] : dst + o;
         }
-        const Key *src = stage ? stage + so : dst + o;
         Key *out = dst + o;
-        // ---- short segments: one lane each
         if (len == 1) {
             if (stage) out[0] = src[0];
         } else if (len > 1 && len <= kLaneSort) {
@@ -1312,17 +1313,46 @@ __global__ void __launch_bounds__(256) k_sort_small(Key *dst, const int64_t *seg
             for (int r = 0; r < kLaneSort; ++r)
                 if (r < len) out[r] = v[r];
         }
-        // ---- the others: the whole warp, one segment at a time
-        unsigned todo = __ballot_sync(kFull, len > kLaneSort);
-        while (todo) {
-            const int l = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t ol = __shfl_sync(kFull, o, l);
-            const int64_t ll = __shfl_sync(kFull, len, l);
-            const int64_t sl = __shfl_sync(kFull, so, l);
-            warp_sort_segment<Key>(dst + ol, stage ? stage + sl : dst + ol, ll, stage != nullptr,
-                                   i0 + l, sbuf[wib], big, nbig, lane);
+        unsigned longer = __ballot_sync(kFull, len > kLaneSort);
+        if (longer && inline_long) {   // many segments per warp: the warp sorts them itself
+            while (longer) {
+                const int l = __ffs(longer) - 1;
+                longer &= longer - 1;
+                const int64_t ol = __shfl_sync(kFull, o, l);
+                const int64_t ll = __shfl_sync(kFull, len, l);
+                const Key *sl = (const Key *)__shfl_sync(kFull, (unsigned long long)src, l);
+                warp_sort_segment<Key>(dst + ol, sl, ll, stage != nullptr, i0 + l, sbuf[wib], big,
+                                       nbig, lane);
+            }
+        } else if (longer) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(nmid, (unsigned long long)__popc(longer));
+            base = __shfl_sync(kFull, base, 0);
+            if (len > kLaneSort) mid[base + __popc(longer & ((1u << lane) - 1u))] = i;
         }
+    }
+}
+
+// One warp per listed segment longer than kLaneSort keys (grid-stride over
+// the list): sorted in registers or in the warp's shared buffer; segments
+// longer than that buffer are copied into place and listed in `big`.
+template <typename Key>
+__global__ void __launch_bounds__(256) k_sort_mid(Key *dst, const int64_t *seg_off,
+                                                  const Key *stage, const int64_t *stage_off,
+                                                  const int64_t *mid,
+                                                  const unsigned long long *nmid, int64_t *big,
+                                                  unsigned long long *nbig) {
+    constexpr int kCapW = kWarpSortBytes / (int)sizeof(Key);
+    __shared__ Key sbuf[8][kCapW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    const int64_t cnt = (int64_t)*nmid;
+    for (int64_t x = (int64_t)blockIdx.x * 8 + wib; x < cnt; x += nw) {
+        const int64_t i = mid[x];
+        const int64_t o = seg_off[i];
+        const int64_t len = seg_off[i + 1] - o;
+        warp_sort_segment<Key>(dst + o, stage ? stage + stage_off[i] : dst + o, len,
+                               stage != nullptr, i, sbuf[wib], big, nbig, lane);
     }
 }
 
@@ -1420,7 +1450,8 @@ im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, c
                               const int64_t *stage_off, void *tmp, size_t tmp_bytes,
                               int64_t *ngiant_host, cudaStream_t st, const char *warp_name,
                               const char *block_name) {
-    // tmp layout: [2 counters][big list nseg][giant list nseg]
+    // tmp layout: [2 counters][big list nseg][giant list nseg]; the giant
+    // list's space and second counter first hold the list for k_sort_mid
     if (tmp_bytes < (size_t)(2 + 2 * nseg) * 8) return IM_ERR_INVALID_ARG;
     unsigned long long *ctr = (unsigned long long *)tmp;
     int64_t *big = (int64_t *)tmp + 2;
@@ -1428,10 +1459,21 @@ im_status segmented_sort_impl(Key *keys, const int64_t *seg_off, int64_t nseg, c
     IM_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), st));
     if (nseg == 0) return IM_OK;
     const int gs = blocks_for((const void *)k_sort_small<Key>, 256, 0);
+    const int gm = blocks_for((const void *)k_sort_mid<Key>, 256, 0);
+    // with at least four groups of 32 segments per warp the longer segments
+    // spread over the warps anyway: each warp sorts its own; with fewer, they
+    // are listed and k_sort_mid gives each its own warp
+    const bool inline_long = nseg >= (int64_t)gs * 8 * 32 * 4;
     {
         KernelTimer kt(st, warp_name);
-        k_sort_small<Key><<<gs, 256, 0, st>>>(keys, seg_off, nseg, stage, stage_off, big, ctr);
+        k_sort_small<Key><<<gs, 256, 0, st>>>(keys, seg_off, nseg, stage, stage_off, giant,
+                                               ctr + 1, inline_long, big, ctr);
+        if (!inline_long)
+            k_sort_mid<Key><<<gm, 256, 0, st>>>(keys, seg_off, stage, stage_off, giant, ctr + 1,
+                                                 big, ctr);
     }
+    IM_CUDA(cudaGetLastError());
+    IM_CUDA(cudaMemsetAsync(ctr + 1, 0, sizeof(unsigned long long), st));
     constexpr int kCap = kBlockSortCap * 4 / (int)sizeof(Key);
     const size_t smem = (size_t)kCap * sizeof(Key);
     IM_TRY(raise_dyn_smem((const void *)k_sort_block<Key, kCap>, smem));

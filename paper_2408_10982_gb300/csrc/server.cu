@@ -9,9 +9,11 @@
 // that arrive while batches are on the GPU wait for the next free worker;
 // with several workers, batches overlap on the device.  With a heavy lane
 // (opts.heavy_members > 0), requests whose estimated RRR members reach that
-// bound run on worker 0 only, and the other workers take the rest in arrival
-// order past them, so a few long queries do not hold up the short ones
-// queued behind them.  A result does not depend on the batch it ran in.
+// bound run on worker 0 only, each by itself through the single-query path
+// (sampling into a pool the worker keeps, then max-k-cover), and the other
+// workers take the rest in arrival order past them, so a few long queries do
+// not hold up the short ones queued behind them.  A result does not depend on
+// the batch it ran in.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -86,6 +88,42 @@ double est_members(im_server *s, const im_query &q) {
     return (double)q.theta * per;
 }
 
+// A heavy request on its own, as im_sample_rrr + im_max_k_cover on a pool of
+// its graph and model that worker 0 keeps between requests (recreated larger
+// when theta or the members outgrow it).  For one large query this is the
+// library's fastest path: the per-query kernels, the whole GPU.
+im_status solve_alone(std::map<std::pair<const im_graph *, int32_t>, im_pool *> &pools,
+                      const im_query &q, int64_t want_entries, int32_t *seeds, im_result *res,
+                      cudaStream_t st) {
+    im_pool *&p = pools[{q.graph, q.model}];
+    want_entries = std::max<int64_t>(want_entries, 1 << 16);
+    im_status r = IM_OK;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        if (p && (p->max_sets < q.theta || p->max_entries < want_entries)) {
+            im_pool_destroy(p);
+            p = nullptr;
+        }
+        if (!p) {
+            r = im_pool_create(q.graph, std::max<int64_t>(q.theta, 1), want_entries, &p);
+            if (r != IM_OK) return r;
+        }
+        r = im_pool_reset(p);
+        if (r != IM_OK) return r;
+        r = im_sample_rrr(q.graph, (im_model)q.model, q.seed, 0, (uint64_t)q.theta, p, st);
+        if (r != IM_ERR_CAPACITY) break;
+        want_entries *= 4;                        // the sets were larger than estimated
+    }
+    if (r != IM_OK) return r;
+    std::vector<int64_t> gains((size_t)q.k);
+    const im_cover_opts *o = q.cover.algo != IM_GREEDY_PLAIN ? &q.cover : nullptr;
+    r = im_max_k_cover(p, q.k, o, seeds, gains.data(), &res->num_seeds, &res->coverage, st);
+    if (r != IM_OK) return r;
+    int64_t theta = 0;
+    r = im_pool_info(p, &theta, &res->entries, nullptr);
+    res->partitions = o && q.cover.algo == IM_RANDGREEDI ? q.cover.partitions : 0;
+    return r;
+}
+
 void worker_main(im_server *s, int32_t wid) {
     cudaSetDevice(s->device);
     const bool any = wid == 0 || s->opts.heavy_members <= 0;   // may this worker run heavy ones
@@ -93,6 +131,7 @@ void worker_main(im_server *s, int32_t wid) {
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     im_batch *b = nullptr;
     im_batch_create(&b);
+    std::map<std::pair<const im_graph *, int32_t>, im_pool *> pools;   // heavy requests alone
     std::vector<uint64_t> ids;
     std::vector<im_query> qs;
     for (;;) {
@@ -116,6 +155,8 @@ void worker_main(im_server *s, int32_t wid) {
         ids.clear();
         qs.clear();
         int64_t mem = 0;
+        bool alone = false;          // worker 0: a heavy request by itself
+        int64_t want_entries = 0;
         for (auto it = s->queue.begin();
              it != s->queue.end() && (int32_t)ids.size() < s->opts.max_batch;) {
             Request &r = s->reqs[*it];
@@ -123,11 +164,22 @@ void worker_main(im_server *s, int32_t wid) {
                 ++it;
                 continue;
             }
+            // the heavy lane runs a heavy request alone, not inside a batch
+            // (a RandGreedi request that leaves its partition count to the
+            // batch still goes through one)
+            const bool by_itself = r.heavy && s->opts.heavy_members > 0 &&
+                                   !(r.q.cover.algo == IM_RANDGREEDI && r.q.cover.partitions <= 0);
+            if (by_itself && !ids.empty()) break;
             if (!ids.empty() && s->mem_in_use + mem + r.footprint > s->opts.mem_budget) break;
             mem += r.footprint;
             ids.push_back(*it);
             qs.push_back(r.q);
             it = s->queue.erase(it);
+            if (by_itself) {
+                alone = true;
+                want_entries = (int64_t)(est_members(s, r.q) * 1.25);
+                break;
+            }
         }
         s->mem_in_use += mem;
         s->in_flight++;
@@ -138,7 +190,9 @@ void worker_main(im_server *s, int32_t wid) {
         std::vector<int32_t> seeds((size_t)qs.size() * kmax);
         std::vector<im_result> res(qs.size());
         const im_status st_batch =
-            im_solve_batch(b, qs.data(), (int32_t)qs.size(), kmax, seeds.data(), nullptr, res.data(), st);
+            alone ? solve_alone(pools, qs[0], want_entries, seeds.data(), res.data(), st)
+                  : im_solve_batch(b, qs.data(), (int32_t)qs.size(), kmax, seeds.data(), nullptr,
+                                   res.data(), st);
         const std::string err = st_batch == IM_OK ? std::string() : std::string(im_last_error());
         // a batch that failed part way may still have work queued on the stream:
         // let it finish before the arena is reused or the worker leaves
@@ -172,6 +226,8 @@ void worker_main(im_server *s, int32_t wid) {
         s->cv_done.notify_all();
         s->cv_work.notify_all();
     }
+    for (auto &kv : pools)
+        if (kv.second) im_pool_destroy(kv.second);
     im_batch_destroy(b);
     cudaStreamDestroy(st);
 }

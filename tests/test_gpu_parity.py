@@ -281,6 +281,22 @@ def test_randgreedi_bucket_stage_variants(im, cluster):
         im.im_tune_set(im.IM_TUNE_RG_CLUSTER, old)
 
 
+@pytest.mark.parametrize("cluster", [0, -1])
+def test_randgreedi_fused_layouts(im, cluster):
+    """One-launch RandGreedi (producers and bucket consumers in one cooperative
+    launch, the consumers reading slots as they are published) under both
+    bucket-stage knob values gives the oracle's result, with 148 and with 100
+    parts."""
+    old = im.im_tune_get(im.IM_TUNE_RG_CLUSTER)
+    im.im_tune_set(im.IM_TUNE_RG_CLUSTER, cluster)
+    try:
+        g = inputs.rmat_graph(1 << 14, 1 << 18, 42, "lt")
+        _rg_compare(im, g, im.IM_LT, 30000, 50, 148, (1, 4), 0.077, True)
+        _rg_compare(im, g, im.IM_LT, 30000, 50, 100, (1, 8), 0.077, True)
+    finally:
+        im.im_tune_set(im.IM_TUNE_RG_CLUSTER, old)
+
+
 def test_randgreedi_large_theta_cluster(im):
     """theta above one block's shared memory: the automatic cluster has >= 2 blocks."""
     g = inputs.rmat_graph(1 << 12, 1 << 16, 5, "lt")
@@ -532,7 +548,7 @@ def test_autotune_picks_allowed_values_and_keeps_results(im):
         G = im.Graph(g)
         opts = im.cover_opts(im.IM_RANDGREEDI, 148, (1, 4), 0.077, 42, False)
         r = im.im_autotune(G.handle, im.IM_LT, 42, 20000, 50, opts)
-        assert r["lt_group"] in (1, 8, 16, 32) and r["index_replicas"] in (1, 2, 4, 8)
+        assert r["lt_group"] in (1, 8, 16, 32) and r["index_replicas"] in (0, 1, 2, 4, 8)
         assert r["rg_evals"] in (1, 2, 4, 8) and r["rg_cluster"] in (0, 1, 2, 4, 8, -1)
         assert im.im_tune_get(im.IM_TUNE_LT_GROUP) == r["lt_group"]
         assert im.im_tune_get(im.IM_TUNE_RG_CLUSTER) == r["rg_cluster"]
