@@ -114,7 +114,7 @@ __device__ __forceinline__ void mark_overflow(const SampleArgs &a, int64_t j, in
 // Philox(s, e >> 2 (low word), e >> 34, coin tag) is below w[e].
 // ---------------------------------------------------------------------------
 template <bool kSmemVis>
-__global__ void __launch_bounds__(kSampleThreads) k_sample_ic(SampleArgs a) {
+__global__ void __launch_bounds__(kSampleThreads, 4) k_sample_ic(SampleArgs a) {
     extern __shared__ uint32_t smem_vis[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wib;
