@@ -124,8 +124,8 @@ def _solve_alone(im, G, model, k, theta, seed, cap_per_set=64):
 def test_batched_mix_256_queries(im):
     """The batched workload (256 queries over R-MAT scales 12..18, IC weighted
     cascade or LT, k in [5, 100], theta in [2^14, 2^20]) in one im_solve_batch
-    call: every query equals the one-query path, and the six smallest queries
-    equal the oracle."""
+    call: every query equals the one-query path; the six smallest queries and
+    the smallest of every (scale, model) pair equal the oracle."""
     specs = inputs.batched_queries(256, 42)
     graphs = {f"rmat{s}": inputs.batched_graph(s, 42) for s in inputs.BATCH_SCALES}
     G = {name: im.Graph(g) for name, g in graphs.items()}
@@ -141,7 +141,14 @@ def test_batched_mix_256_queries(im):
         assert gains.tolist() == g1.tolist(), q
         assert cov == c1 and entries == e1, q
     order = sorted(range(len(specs)), key=lambda i: (specs[i].theta << 8) + int(specs[i].graph[4:]))
-    for i in order[:6]:
+    picked, seen = list(order[:6]), set()
+    for i in order:                         # the smallest query of every (scale, model)
+        key = (specs[i].graph, specs[i].model)
+        if key not in seen:
+            seen.add(key)
+            if i not in picked:
+                picked.append(i)
+    for i in picked:
         q = specs[i]
         g = graphs[q.graph]
         pool = O.sample(q.model, g, q.seed, 0, q.theta)
@@ -152,16 +159,19 @@ def test_batched_mix_256_queries(im):
         assert cov == rc.coverage and entries == pool.members.size, q
 
 
-def test_served_trace_results_equal_alone(im):
+@pytest.mark.parametrize("workers,heavy", [(2, 0), (3, 1 << 22)])
+def test_served_trace_results_equal_alone(im, workers, heavy):
     """Continuous batching on the served trace (Poisson arrivals, mean 200/s,
     queries drawn like the batched mix): requests are submitted at their
     arrival times while earlier ones run, and every served result equals the
-    one-query path."""
+    one-query path; with a heavy lane as well (the largest queries alone on
+    worker 0, the rest batched by the others)."""
     import time
     specs = inputs.served_trace(256, 42, orkut_frac=0.0)
     graphs = {f"rmat{s}": inputs.batched_graph(s, 42) for s in inputs.BATCH_SCALES}
     G = {name: im.Graph(g) for name, g in graphs.items()}
-    srv = im.im_server_create(workers=2, max_batch=64, mem_budget=96 << 30)
+    srv = im.im_server_create(workers=workers, max_batch=64, mem_budget=96 << 30,
+                              heavy_members=heavy)
     tickets = []
     try:
         t0 = time.perf_counter()
