@@ -974,6 +974,7 @@ __global__ void k_lt_index_small(const int64_t *in_off, const int32_t *in_src, c
             leaf[i] = (c << 31) | (unsigned long long)(uint32_t)in_src[i];
         }
         if (c > (1ull << 32)) atomicExch(invalid, 1);
+        if (d > 0 && !(same && w0 != 0u)) invalid[2] = 1;   // the cut points are needed
         vrec[v] = make_uint4((uint32_t)b, (uint32_t)d, (uint32_t)tree_off[v], same ? w0 : 0u);
     }
 }
@@ -1003,6 +1004,7 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
         }
         same = __all_sync(kFull, same);
         if (lane == 0 && carry > (1ull << 32)) atomicExch(invalid, 1);
+        if (lane == 0 && !(same && w0 != 0u)) invalid[2] = 1;
         int L = 0;
         for (int64_t t = d; t > 32; t = (t + 31) >> 5) ++L;
         if (lane == 0)
@@ -1067,6 +1069,7 @@ __global__ void __launch_bounds__(256) k_lt_index_block(
         }
         same = __syncthreads_and(same) != 0;
         if (tid == 0 && carry > (1ull << 32)) atomicExch(invalid, 1);
+        if (tid == 0 && !(same && w0 != 0u)) invalid[2] = 1;
         int L = 0;
         for (int64_t t = d; t > 32; t = (t + 31) >> 5) ++L;
         if (tid == 0)
@@ -1503,7 +1506,8 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
         cudaStream_t st;
         int32_t *sizes = nullptr, *big = nullptr;
         int64_t *toff = nullptr;
-        int *flags = nullptr;   // [0] weights of some vertex sum above 2^32, [1] listed vertices
+        int *flags = nullptr;   // [0] weights of some vertex sum above 2^32, [1] listed
+                                // vertices, [2] some vertex needs the cut points
         ~Temps() {
             for (void *p : {(void *)sizes, (void *)big, (void *)toff, (void *)flags})
                 if (p) cudaFreeAsync(p, st);
@@ -1525,8 +1529,8 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
     IM_CUDA(cudaMallocAsync((void **)&t.sizes, (size_t)n * 4, st));
     IM_CUDA(cudaMallocAsync((void **)&t.big, (size_t)big_cap * 4, st));
     IM_CUDA(cudaMallocAsync((void **)&t.toff, (size_t)(n + 1) * 8 + scan_tmp_bytes(n) + 256, st));
-    IM_CUDA(cudaMallocAsync((void **)&t.flags, 2 * sizeof(int), st));
-    IM_CUDA(cudaMemsetAsync(t.flags, 0, 2 * sizeof(int), st));
+    IM_CUDA(cudaMallocAsync((void **)&t.flags, 3 * sizeof(int), st));
+    IM_CUDA(cudaMemsetAsync(t.flags, 0, 3 * sizeof(int), st));
     {
         KernelTimer kt(st, "lt_index");
         k_lt_tree_sizes<<<num_sms() * 4, 256, 0, st>>>(g->in_off, n, t.sizes, t.big, t.flags + 1);
@@ -1557,16 +1561,21 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
                 t.flags);
     }
     IM_CUDA(cudaGetLastError());
-    IM_CUDA(cudaMalloc(&x.guide, (size_t)std::max<int64_t>(m, 1) * sizeof(uint4)));
-    if (m > 0) {
-        KernelTimer kt(st, "lt_index");
-        k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, x.leaf, x.vrec, n, m, x.guide);
-    }
-    IM_CUDA(cudaGetLastError());
-    int invalid = 0;
-    IM_CUDA(cudaMemcpyAsync(&invalid, t.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hflags[3] = {0, 0, 0};
+    IM_CUDA(cudaMemcpyAsync(hflags, t.flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaStreamSynchronize(st));
-    g->lt_valid = invalid ? 0 : 1;
+    // the cut points serve only vertices whose in-edges weigh differently (or
+    // all zero): a graph without such vertices (1/in-degree weights) has none
+    if (hflags[2] && m > 0) {
+        IM_CUDA(cudaMalloc(&x.guide, (size_t)m * sizeof(uint4)));
+        {
+            KernelTimer kt(st, "lt_index");
+            k_lt_guide<<<num_sms() * 8, 256, 0, st>>>(g->in_off, x.leaf, x.vrec, n, m, x.guide);
+        }
+        IM_CUDA(cudaGetLastError());
+        IM_CUDA(cudaStreamSynchronize(st));
+    }
+    g->lt_valid = hflags[0] ? 0 : 1;
     g->lt_tree = x.tree;
     g->lt_vrec = x.vrec;
     g->lt_guide = x.guide;
