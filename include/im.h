@@ -77,8 +77,8 @@ typedef enum { IM_AGG_STREAM = 0, IM_AGG_GREEDY = 1 } im_aggregator;
  *                   one cooperative launch with the aggregator consuming seeds
  *                   as they are produced (streaming overlap, bucket bitmaps in
  *                   global memory); 0 runs them as two launches, the second
- *                   keeping each bucket's bitmap in the shared memory of a
- *                   thread-block cluster (see IM_TUNE_RG_CLUSTER).  Results
+ *                   a bucket stage laid out as IM_TUNE_RG_CLUSTER says (by
+ *                   default one 64-bit bucket mask per RRR set).  Results
  *                   are identical.
  *   aggregator      RandGreedi only: IM_AGG_STREAM (0) aggregates with the
  *                   streaming buckets of Alg. 5 (Sec. 3.3); IM_AGG_GREEDY (1)
@@ -520,9 +520,12 @@ typedef struct {
 
 typedef struct im_server im_server;
 im_status im_server_create(const im_server_opts *opts, im_server **out);
-/* Finishes every queued request, then stops the workers. */
+/* Finishes every queued request, then stops the workers and frees their
+ * batch arenas and pools. */
 im_status im_server_destroy(im_server *s);
-/* Queues a query (copied); *ticket identifies it.  The graph must stay alive. */
+/* Queues a query (copied); *ticket identifies it.  The graph must stay alive
+ * until the server is destroyed (the heavy lane keeps a pool per graph and
+ * model until then). */
 im_status im_server_submit(im_server *s, const im_query *q, uint64_t *ticket);
 /* Result of a finished request, then forgotten: seeds int32[k] (host), number
  * of seeds, coverage, and the latency from submission to completion.
