@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
 constexpr int kLT1Threads = 256;
 constexpr int kBloomWords = 32;              // 1024 bits per walk
 constexpr int64_t kQueueCapLT1 = 512;
-constexpr unsigned kLT1Chunk = 64;           // sample indices a warp takes at once
+constexpr unsigned kLT1Chunk = 32;           // sample indices a warp takes at once
 
 __device__ __forceinline__ uint32_t bloom_h1(uint32_t u) { return (u * 0x9E3779B1u) >> 22; }
 __device__ __forceinline__ uint32_t bloom_h2(uint32_t u) {
