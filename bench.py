@@ -67,11 +67,11 @@ WORKLOAD = ("rmat20-lt: R-MAT scale 20 (1,048,576 vertices, 16,777,216 edges, a/
             "+ RandGreedi (148 partitions, streamed top ceil(k/4), delta=0.077)")
 # DRAM bytes per launch from an ncu capture, valid while the kernel source is
 # unchanged (sha256 of the kernel's source text, see kernel_sha).  k_sample_lt1 was captured on
-# the same graph at theta = 1,048,576 (42.82 M walk steps, 2.8387 GB read +
+# the same graph at theta = 1,048,576 (42.82 M walk steps, 2.5637 GB read +
 # written, profiles/ncu_sample_lt1_rmat20_theta1M.txt); traffic grows with the
-# walk steps, so a full launch (171.49 M steps) moves 2.8387 * 171.49 / 42.82 GB.
-TRAFFIC: dict = {"sample_lt": {"src_sha": "2829223a0e398845",
-                               "bytes_per_launch": int(2.8387e9 * 171.49 / 42.82)}}
+# walk steps, so a full launch (171.49 M steps) moves 2.5637 * 171.49 / 42.82 GB.
+TRAFFIC: dict = {"sample_lt": {"src_sha": "5dfa6a69246f81f9",
+                               "bytes_per_launch": int(2.5637e9 * 171.49 / 42.82)}}
 
 
 def parse():

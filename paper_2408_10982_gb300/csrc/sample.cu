@@ -679,13 +679,26 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
 // the vertex weigh u (1/in-degree weights, for one), else one guide entry (see
 // k_lt_guide), with a binary search over the running sums only when the draw
 // lies past the guide's edge.  The revisit test goes through a 1024-bit Bloom filter of
-// the walk in shared memory (two hashes); only a hit is checked exactly, by
-// the whole warp scanning that walk's path.  Finished walks are copied to the
-// stage by the whole warp as well, after one warp-wide reservation.
+// the walk in shared memory (two hashes); a walk whose pick hits the filter
+// waits (takes no step) until kLT1Flush walks of its warp wait, or every active
+// one does, and the whole warp then checks them exactly, scanning kLT1Group of
+// their paths together so that those loads are in flight at once.  Finished
+// walks are copied to the stage by the whole warp as well, kLT1Group paths at
+// a time, after one warp-wide reservation.
+// A warp takes sample indices kLT1Chunk at a time, and all its lanes then draw
+// the roots of that chunk together (one Philox call each) into a per-warp ring
+// in shared memory, from which a lane starting a walk reads its root.
+// Waiting changes no draw: a walk's steps are the same whenever they run.
 constexpr int kLT1Threads = 256;
+constexpr int kLT1Warps = kLT1Threads / 32;
 constexpr int kBloomWords = 32;              // 1024 bits per walk
 constexpr int64_t kQueueCapLT1 = 512;
-constexpr unsigned kLT1Chunk = 32;           // sample indices a warp takes at once
+constexpr unsigned kLT1Chunk = 32;           // sample indices a warp takes at once (one per lane)
+constexpr int kLT1Flush = 2;                 // flagged walks that trigger the exact checks
+constexpr int kLT1Group = 2;                 // paths scanned or copied together
+// The work items of one launch stay below this count, so that the warp's chunk
+// bounds fit 32 bits (a larger job takes the grouped kernel).
+constexpr int64_t kLT1MaxCount = (1ll << 32) - (1ll << 28);
 
 __device__ __forceinline__ uint32_t bloom_h1(uint32_t u) { return (u * 0x9E3779B1u) >> 22; }
 __device__ __forceinline__ uint32_t bloom_h2(uint32_t u) {
@@ -728,59 +741,93 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first() {
 // CP (IM_TUNE_LT_CACHE): 0 plain loads; 1 the vertex records (n x 16 B, read
 // at every step) are kept in L2 ahead of other lines (evict_last); 2 as 1, and
 // the cut points (m x 16 B, mostly single-use) leave L2 first (evict_first).
+// Launched with a.count <= kLT1MaxCount.  Four blocks per SM: the 63 registers
+// the grouped scans want, with no spills (five blocks at 48 registers measured
+// slower).
 template <int CP>
-__global__ void __launch_bounds__(kLT1Threads, 5) k_sample_lt1(SampleArgs a) {
+__global__ void __launch_bounds__(kLT1Threads, 4) k_sample_lt1(SampleArgs a) {
     extern __shared__ uint32_t bloom[];          // [kBloomWords][kLT1Threads]
-    const uint64_t pol_v = CP >= 1 ? l2_policy_evict_last() : 0ull;
-    const uint64_t pol_c = CP >= 2 ? l2_policy_evict_first() : 0ull;
-    const int lane = threadIdx.x & 31;
+    // roots, sample ids and query indices of the warp's last two chunks
+    __shared__ uint32_t ring_root[kLT1Warps][2 * kLT1Chunk];
+    __shared__ uint32_t ring_s[kLT1Warps][2 * kLT1Chunk];
+    __shared__ int32_t ring_q[kLT1Warps][2 * kLT1Chunk];
+    // per warp: examined edges and algorithmic bytes of its finished walks
+    __shared__ unsigned long long wsum[kLT1Warps][2];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *bl = bloom + threadIdx.x;
-    const int64_t slot0 = (int64_t)blockIdx.x * kLT1Threads + (threadIdx.x & ~31);
-    int32_t *q = a.queues + (slot0 + lane) * a.qcap;
+    int32_t *q = a.queues + ((int64_t)blockIdx.x * kLT1Threads + threadIdx.x) * a.qcap;
+    if (lane == 0) {
+        wsum[wib][0] = 0ull;
+        wsum[wib][1] = 0ull;
+    }
+    // with one query in the launch, every walk has the same graph and key
+    const bool one_query = a.nq == 1;
+    const uint4 *vrec = one_query ? a.qv[0].lt_vrec : nullptr;
+    const int32_t *srcs = one_query ? a.qv[0].in_src : nullptr;
+    uint32_t k0 = one_query ? seed_lo(a.qv[0].seed) : 0u;
+    uint32_t k1 = one_query ? seed_hi(a.qv[0].seed) : 0u;
     bool active = false, exhausted = false;
-    int64_t j = 0;
-    uint32_t s = 0, cur = 0, k0 = 0, k1 = 0;
-    const uint4 *vrec = nullptr, *guide = nullptr;
-    const unsigned long long *leaf = nullptr;
-    const int32_t *srcs = nullptr;
-    int32_t len = 0;
-    unsigned long long sexam = 0, exam = 0, abytes = 0;
+    bool pend = false;                           // waiting for an exact revisit check of u
+    uint32_t j = 0, s = 0, cur = 0, u = 0;
+    int32_t qi = 0, len = 0;
+    unsigned long long sexam = 0;
     uint32_t sbytes = 0;
-    // the warp's current chunk of sample indices [wnext, wend), taken from the
-    // global counter kLT1Chunk at a time (warp-uniform)
-    unsigned long long wnext = 0, wend = 0;
+    // the warp's current chunk is [wend - kLT1Chunk, wend); [wnext, wend) is not
+    // taken yet; the chunk's roots are in half `half` of the ring (warp-uniform)
+    uint32_t wnext = 0, wend = 0;
+    int half = 1;
+    __syncwarp();
     for (;;) {
         // ---- lanes without a walk take the next samples of the warp's chunk
         const bool want = !active && !exhausted;
         const unsigned need = __ballot_sync(kFull, want);
         if (need) {
-            const unsigned nneed = (unsigned)__popc(need);
-            const unsigned rank = __popc(need & ((1u << lane) - 1u));
-            const unsigned long long avail = wend - wnext;
-            unsigned long long jw = wnext + rank;
+            const uint32_t nneed = (uint32_t)__popc(need);
+            const uint32_t rank = (uint32_t)__popc(need & ((1u << lane) - 1u));
+            const uint32_t avail = wend - wnext;
+            uint32_t jw = wnext + rank;
+            uint32_t cb = wend - kLT1Chunk;          // first index of jw's chunk
+            int hw = half;                           // and the ring half holding it
             if (avail < nneed) {                     // the rest of this chunk, then a new one
-                unsigned long long nb = 0;
-                if (lane == 0) nb = atomicAdd(a.work, (unsigned long long)kLT1Chunk);
-                nb = __shfl_sync(kFull, nb, 0);
-                if (rank >= avail) jw = nb + (rank - avail);
+                unsigned long long nb64 = 0;
+                if (lane == 0) nb64 = atomicAdd(a.work, (unsigned long long)kLT1Chunk);
+                const uint32_t nb = (uint32_t)__shfl_sync(kFull, nb64, 0);
+                half ^= 1;
+                const uint32_t jc = nb + (uint32_t)lane;
+                if ((int64_t)jc < a.count) {         // lane draws the root of sample nb + lane
+                    const int64_t jj = a.list ? a.list[jc] : (int64_t)jc;
+                    const int qc = one_query ? 0 : find_query(a, jj);
+                    const QueryView &V = a.qv[qc];
+                    const uint32_t sc = V.first + (uint32_t)(jj - __ldg(a.qstart + qc));
+                    ring_root[wib][half * kLT1Chunk + lane] = rrr_root(V.seed, sc, V.n);
+                    ring_s[wib][half * kLT1Chunk + lane] = sc;
+                    ring_q[wib][half * kLT1Chunk + lane] = qc;
+                }
+                __syncwarp();
+                if (rank >= avail) {
+                    jw = nb + (rank - avail);
+                    cb = nb;
+                    hw = half;
+                }
                 wnext = nb + (nneed - avail);
                 wend = nb + kLT1Chunk;
             } else {
                 wnext += nneed;
             }
             if (want) {
-                if (jw < (unsigned long long)a.count) {
-                    j = a.list ? a.list[jw] : (int64_t)jw;
-                    const int qi = find_query(a, j);
-                    const QueryView &V = a.qv[qi];
-                    vrec = V.lt_vrec;
-                    guide = V.lt_guide;
-                    leaf = V.lt_leaf;
-                    srcs = V.in_src;
-                    k0 = seed_lo(V.seed);
-                    k1 = seed_hi(V.seed);
-                    s = V.first + (uint32_t)(j - __ldg(a.qstart + qi));
-                    cur = rrr_root(V.seed, s, V.n);
+                if ((int64_t)jw < a.count) {
+                    const int e = hw * (int)kLT1Chunk + (int)(jw - cb);
+                    j = a.list ? (uint32_t)a.list[jw] : jw;
+                    cur = ring_root[wib][e];
+                    s = ring_s[wib][e];
+                    qi = ring_q[wib][e];
+                    if (!one_query) {
+                        const QueryView &V = a.qv[qi];
+                        vrec = V.lt_vrec;
+                        srcs = V.in_src;
+                        k0 = seed_lo(V.seed);
+                        k1 = seed_hi(V.seed);
+                    }
                     q[0] = (int32_t)cur;
 #pragma unroll
                     for (int w = 0; w < kBloomWords; ++w) bl[w * kLT1Threads] = 0u;
@@ -796,16 +843,18 @@ __global__ void __launch_bounds__(kLT1Threads, 5) k_sample_lt1(SampleArgs a) {
         }
         if (!__any_sync(kFull, active)) break;
 
-        // ---- one step of every active walk
-        bool picked = false;
-        uint32_t u = 0;
-        if (active) {
+        // ---- one step of every active walk that is not waiting for its revisit check
+        bool ending = false, accept = false;
+        if (active && !pend) {
             const uint32_t x = philox4x32_10(make_uint4(s, cur, 0u, kStreamPick), k0, k1).x;
-            const uint4 vr = CP >= 1 ? ldg_policy(vrec + cur, pol_v) : __ldg(vrec + cur);
+            // (the L2 policies are made where they are used: one instruction,
+            // and no registers held across the loop)
+            const uint4 vr =
+                CP >= 1 ? ldg_policy(vrec + cur, l2_policy_evict_last()) : __ldg(vrec + cur);
             const uint32_t d = vr.y;
             int64_t e = -1;
             sbytes += 16u;                           // vertex record
-            if (vr.w != 0u) {                        // equal in-weights u: edge floor(x / u)
+            if (vr.w != 0u) {                        // equal in-weights: edge floor(x / weight)
                 const uint32_t ei = x / vr.w;
                 if (ei < d) {
                     e = ei;
@@ -813,14 +862,16 @@ __global__ void __launch_bounds__(kLT1Threads, 5) k_sample_lt1(SampleArgs a) {
                     sbytes += 4u;                    // source of the pick
                 }
             } else if (d > 0) {
-                const uint4 *gp = guide + vr.x + __umulhi(x, d);
-                const uint4 gv = CP >= 2 ? ldg_policy(gp, pol_c) : __ldg(gp);
+                const QueryView &V = a.qv[qi];
+                const uint4 *gp = V.lt_guide + vr.x + __umulhi(x, d);
+                const uint4 gv = CP >= 2 ? ldg_policy(gp, l2_policy_evict_first()) : __ldg(gp);
                 const unsigned long long cum = ((unsigned long long)gv.y << 32) | gv.x;
                 sbytes += 16u;                       // cut point
                 if ((unsigned long long)x < cum) {
                     e = gv.w;
                     u = gv.z;
                 } else {
+                    const unsigned long long *leaf = V.lt_leaf;
                     uint32_t lo = gv.w + 1, hi = d;  // first edge past the guide's with x < sum
                     while (lo < hi) {
                         const uint32_t mid = (lo + hi) >> 1;
@@ -835,28 +886,57 @@ __global__ void __launch_bounds__(kLT1Threads, 5) k_sample_lt1(SampleArgs a) {
                     }
                 }
             }
-            picked = e >= 0;
-            sexam += picked ? (unsigned long long)(e + 1) : (unsigned long long)d;
+            sexam += e >= 0 ? (unsigned long long)(e + 1) : (unsigned long long)d;
+            if (e < 0) ending = true;                // no in-edge picked: the walk stops
+            else if (bloom_has(bl, u)) pend = true;  // maybe a revisit: check exactly
+            else accept = true;
         }
-        // ---- revisit test: Bloom filter, then an exact scan of the flagged walks
-        unsigned hits = __ballot_sync(kFull, picked && bloom_has(bl, u));
-        bool seen = false;
-        if (hits) {
-            __syncwarp();
+        // ---- exact revisit checks of the flagged walks, once kLT1Flush of them wait
+        // (or every active walk does); kLT1Group paths are scanned together
+        const unsigned pm = __ballot_sync(kFull, pend);
+        if (pm && (__popc(pm) >= kLT1Flush || pm == __ballot_sync(kFull, active))) {
+            bool seen = false;
+            unsigned rest = pm;
             do {
-                const int l = __ffs(hits) - 1;
-                hits &= hits - 1;
-                const int32_t ul = __shfl_sync(kFull, (int32_t)u, l);
-                const int32_t ll = __shfl_sync(kFull, len, l);
-                const int32_t *ql = a.queues + (slot0 + l) * a.qcap;
-                bool f = false;
-                for (int32_t i = lane; i < ll; i += 32) f |= __ldcg(ql + i) == ul;
-                const bool any = __any_sync(kFull, f);
-                if (lane == l) seen = any;
-            } while (hits);
+                int l[kLT1Group];
+#pragma unroll
+                for (int g = 0; g < kLT1Group; ++g) {   // lanes of the group; repeats when fewer
+                    l[g] = rest ? __ffs(rest) - 1 : l[0];
+                    rest &= rest - 1u;
+                }
+                int32_t ug[kLT1Group], lg[kLT1Group];
+                int32_t lmax = 0;
+#pragma unroll
+                for (int g = 0; g < kLT1Group; ++g) {
+                    ug[g] = __shfl_sync(kFull, (int32_t)u, l[g]);
+                    lg[g] = __shfl_sync(kFull, len, l[g]);
+                    lmax = max(lmax, lg[g]);
+                }
+                bool f[kLT1Group];
+#pragma unroll
+                for (int g = 0; g < kLT1Group; ++g) f[g] = false;
+                for (int32_t i = lane; i < lmax; i += 32) {
+                    int32_t v[kLT1Group];
+#pragma unroll
+                    for (int g = 0; g < kLT1Group; ++g)      // lane l[g]'s path entry i
+                        v[g] = i < lg[g] ? __ldcg(q + (int64_t)(l[g] - lane) * a.qcap + i) : -1;
+#pragma unroll
+                    for (int g = 0; g < kLT1Group; ++g) f[g] |= v[g] == ug[g];
+                }
+#pragma unroll
+                for (int g = 0; g < kLT1Group; ++g) {
+                    const bool any = __any_sync(kFull, f[g]);
+                    if (lane == l[g]) seen = any;
+                }
+            } while (rest);
+            if (pend) {
+                if (seen) ending = true;             // a revisit: the walk stops
+                else accept = true;
+                pend = false;
+            }
         }
         bool ovf = false;
-        if (picked && !seen) {
+        if (accept) {
             if (len < a.qcap) {
                 q[len] = (int32_t)u;
                 bloom_add(bl, u);
@@ -864,16 +944,14 @@ __global__ void __launch_bounds__(kLT1Threads, 5) k_sample_lt1(SampleArgs a) {
                 sbytes += 4u;                        // member write
                 cur = u;
             } else {
-                ovf = true;
+                ovf = true;                          // longer than the queue: second pass
+                ending = true;
+                a.sizes[j] = -1;
+                a.stage_off[j] = 0;
+                a.ovf_list[atomicAdd(a.ovf_count, 1ull)] = (int64_t)j;
             }
         }
-        const bool ending = active && !(picked && !seen && !ovf);
-        if (ending && ovf) {                         // longer than the queue: second pass
-            a.sizes[j] = -1;
-            a.stage_off[j] = 0;
-            a.ovf_list[atomicAdd(a.ovf_count, 1ull)] = j;
-        }
-        // ---- finished walks go to the stage
+        // ---- finished walks go to the stage, kLT1Group paths copied together
         const bool emit = ending && !ovf;
         unsigned em = __ballot_sync(kFull, emit);
         if (em) {
@@ -888,8 +966,8 @@ __global__ void __launch_bounds__(kLT1Threads, 5) k_sample_lt1(SampleArgs a) {
                 if (fits) {
                     a.stage_off[j] = (int64_t)base + incl - my;
                     a.sizes[j] = len;
-                    exam += sexam;
-                    abytes += sbytes;
+                    atomicAdd(&wsum[wib][0], sexam);
+                    atomicAdd(&wsum[wib][1], (unsigned long long)sbytes);
                 } else {
                     raise_status(a.status, kDevStageOverflow);
                     a.sizes[j] = 0;
@@ -899,22 +977,39 @@ __global__ void __launch_bounds__(kLT1Threads, 5) k_sample_lt1(SampleArgs a) {
             if (fits) {
                 __syncwarp();
                 do {
-                    const int l = __ffs(em) - 1;
-                    em &= em - 1;
-                    const int32_t ll = __shfl_sync(kFull, len, l);
-                    const int64_t pl = (int64_t)base + __shfl_sync(kFull, incl - my, l);
-                    const int32_t *ql = a.queues + (slot0 + l) * a.qcap;
-                    for (int32_t i = lane; i < ll; i += 32) a.stage[pl + i] = __ldcg(ql + i);
+                    int l[kLT1Group];
+#pragma unroll
+                    for (int g = 0; g < kLT1Group; ++g) {
+                        l[g] = em ? __ffs(em) - 1 : l[0];
+                        em &= em - 1u;
+                    }
+                    int32_t lg[kLT1Group], og[kLT1Group];
+                    int32_t lmax = 0;
+#pragma unroll
+                    for (int g = 0; g < kLT1Group; ++g) {
+                        lg[g] = __shfl_sync(kFull, len, l[g]);
+                        og[g] = __shfl_sync(kFull, incl - my, l[g]);   // offset from base
+                        lmax = max(lmax, lg[g]);
+                    }
+                    for (int32_t i = lane; i < lmax; i += 32) {
+                        int32_t v[kLT1Group];
+#pragma unroll
+                        for (int g = 0; g < kLT1Group; ++g)
+                            v[g] = i < lg[g] ? __ldcg(q + (int64_t)(l[g] - lane) * a.qcap + i) : 0;
+#pragma unroll
+                        for (int g = 0; g < kLT1Group; ++g)
+                            if (i < lg[g]) a.stage[(int64_t)base + og[g] + i] = v[g];
+                    }
                 } while (em);
             }
         }
         if (ending) active = false;
         __syncwarp();
     }
-    exam = warp_sum<unsigned long long>(exam);
-    abytes = warp_sum<unsigned long long>(abytes);
-    if (lane == 0 && exam) atomicAdd(a.examined, exam);
-    if (lane == 0 && abytes) atomicAdd(a.alg_bytes, abytes);
+    if (lane == 0) {
+        if (wsum[wib][0]) atomicAdd(a.examined, wsum[wib][0]);
+        if (wsum[wib][1]) atomicAdd(a.alg_bytes, wsum[wib][1]);
+    }
 }
 
 // LT search index.  vrec[v] = {eb, d, tree offset | L << 28, u} with L the
@@ -1615,7 +1710,8 @@ im_status run_sampling(const SamplingJob &job, const std::function<im_status(siz
     const int64_t vis_words = (n + 31) / 32;
 
     // launch shape: persistent, occupancy-sized
-    const int G = model == IM_LT ? (int)tune_value(IM_TUNE_LT_GROUP) : 32;
+    int G = model == IM_LT ? (int)tune_value(IM_TUNE_LT_GROUP) : 32;
+    if (G == 1 && cnt > kLT1MaxCount) G = 32;        // chunk bounds of k_sample_lt1 are 32-bit
     const int lt_cache = (int)tune_value(IM_TUNE_LT_CACHE);
     const bool lt1 = model == IM_LT && G == 1;      // one walk per thread
     const void *kern = model == IM_LT
