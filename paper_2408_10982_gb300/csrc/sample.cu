@@ -273,41 +273,14 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_sample_ic(SampleArgs a) {
 constexpr int kICBigThreads = 1024;
 constexpr int kICBigU = 2;          // edge groups per lane in flight (k_sample_ic_big)
 
-// One group of four in-edges of sample s: coins, liveness, visited marks;
-// returns the fresh sources in src[] and their bits.
-// Coins of edge group g (edges 4g .. 4g+3 inside [eb, ee)) from its loaded
-// weights wv and sources sv; marks the live edges' fresh sources visited.
+// One group of four in-edges of sample s: coins of edge group g (edges
+// 4g .. 4g+3 inside [eb, ee)) against its loaded weights wv, with sources sv;
+// marks the live edges' fresh sources visited and returns their bits (the
+// sources in src[]).
 __device__ __forceinline__ unsigned ic_group_loaded(const uint4 wv, const int4 sv, int64_t g,
                                                     int64_t eb, int64_t ee, uint32_t s,
                                                     uint32_t k0, uint32_t k1, uint32_t *vis,
                                                     int32_t (&src)[4]) {
-    const uint4 coin = philox4x32_10(
-        make_uint4(s, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), kStreamCoin), k0, k1);
-    const uint32_t cv[4] = {coin.x, coin.y, coin.z, coin.w};
-    const uint32_t wq[4] = {wv.x, wv.y, wv.z, wv.w};
-    src[0] = sv.x;
-    src[1] = sv.y;
-    src[2] = sv.z;
-    src[3] = sv.w;
-    unsigned fresh = 0;
-    const int64_t e0 = g << 2;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int64_t e = e0 + c;
-        if (e >= eb && e < ee && cv[c] < wq[c]) {
-            const uint32_t u = (uint32_t)src[c];
-            const uint32_t bit = 1u << (u & 31);
-            if (!(atomicOr(&vis[u >> 5], bit) & bit)) fresh |= 1u << c;
-        }
-    }
-    return fresh;
-}
-
-__device__ __forceinline__ unsigned ic_group(const uint32_t *wgt, const int32_t *in_src, int64_t g,
-                                             int64_t eb, int64_t ee, uint32_t s, uint32_t k0,
-                                             uint32_t k1, uint32_t *vis, int32_t (&src)[4]) {
-    const uint4 wv = __ldg(reinterpret_cast<const uint4 *>(wgt) + g);
-    const int4 sv = __ldg(reinterpret_cast<const int4 *>(in_src) + g);
     const uint4 coin = philox4x32_10(
         make_uint4(s, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), kStreamCoin), k0, k1);
     const uint32_t cv[4] = {coin.x, coin.y, coin.z, coin.w};
