@@ -123,42 +123,54 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region:
+    the sampler is running (its first line read) before the region starts,
+    every line is stamped when it arrives, and only the lines stamped inside
+    the region are summarised."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
 
-    def start(self):
+    def start(self, wait_s: float = 10.0):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t_end = time.perf_counter() + wait_s
+        while not self.lines and self.proc.poll() is None and time.perf_counter() < t_end:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self) -> dict:
+    def stop(self, t0: float, t1: float) -> dict:
+        """Summary of the samples stamped in [t0, t1] (host perf_counter times
+        of the timed region's start and end)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(self.INTERVAL_MS / 1000.0)  # the sample that closes the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1 + self.INTERVAL_MS / 1000.0]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -172,7 +184,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "interval_ms": self.INTERVAL_MS}
 
 
 def kernel_sha(file: str, kernel: str) -> str:
@@ -316,6 +329,7 @@ def run_ours(args):
     nvtx = getattr(torch.cuda, "nvtx", None)
     if nvtx:
         nvtx.range_push("timed")             # lets ncu select the timed launches (--nvtx)
+    t_region = time.perf_counter()
     ev0.record(stream)
     for _ in range(args.steps):
         step()
@@ -323,9 +337,10 @@ def run_ours(args):
     if nvtx:
         nvtx.range_pop()
     torch.cuda.synchronize()
+    t_region_end = time.perf_counter()
     if dist:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_region, t_region_end)
     im.im_profile_enable(False)
     prof = im.im_profile_read()
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
