@@ -9,9 +9,10 @@
 // one 16-byte load of weights and one of sources per group.  Sets longer than
 // the warp's queue are re-run by k_sample_ic_big, one block per sample.  LT:
 // k_sample_lt1 (default) runs one walk per thread; the picked in-edge (first
-// edge whose running weight sum exceeds the draw) comes from a cut-point table
-// in O(1) expected loads, and revisits are tested through a per-walk Bloom
-// filter.  k_sample_lt<G> runs a walk per group of G lanes over a fanout-32
+// edge whose running weight sum exceeds the draw) comes from one division when
+// the vertex's in-edges weigh the same, else from a cut-point table in O(1)
+// expected loads, and revisits are tested through a per-walk Bloom filter
+// (flagged walks are checked exactly, two at a time).  k_sample_lt<G> runs a walk per group of G lanes over a fanout-32
 // search tree (a tuning-knob alternative, and the second pass for walks longer
 // than the thread kernel's queue).  The LT index they read (running sums,
 // tree, cut points) is built once per graph by build_lt_index: in-lists of up
