@@ -12,12 +12,14 @@
 // edge whose running weight sum exceeds the draw) comes from one division when
 // the vertex's in-edges weigh the same, else from a cut-point table in O(1)
 // expected loads, and revisits are tested through a per-walk Bloom filter
-// (flagged walks are checked exactly, two at a time).  k_sample_lt<G> runs a walk per group of G lanes over a fanout-32
+// (flagged walks are checked exactly, two at a time).  k_sample_lt<G> runs a
+// walk per group of G lanes, picking by the same division or over a fanout-32
 // search tree (a tuning-knob alternative, and the second pass for walks longer
-// than the thread kernel's queue).  The LT index they read (running sums,
-// tree, cut points) is built once per graph by build_lt_index: in-lists of up
-// to 32 edges get their running sums from one thread each, up to 1024 from a
-// warp, longer ones from a block.
+// than the thread kernel's queue).  The LT index they read (vertex records;
+// running sums, tree and cut points only when some vertex's in-edges weigh
+// differently) is built once per graph by build_lt_index: in-lists of up to 32
+// edges get their running sums from one thread each, up to 1024 from a warp,
+// longer ones from a block.
 #include <algorithm>
 #include <mutex>
 
@@ -493,6 +495,7 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
     uint32_t s = 0, cur = 0, k0 = 0, k1 = 0;
     const uint4 *vrec = nullptr;
     const unsigned long long *leaf_arr = nullptr, *tree = nullptr;
+    const int32_t *srcs = nullptr;
     int32_t len = 0;
     unsigned long long sexam = 0;
     uint32_t sbytes = 0;   // flushed into abytes before it can wrap
@@ -508,6 +511,7 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
                 vrec = V.lt_vrec;
                 leaf_arr = V.lt_leaf;
                 tree = V.lt_tree;
+                srcs = V.in_src;
                 k0 = seed_lo(V.seed);
                 k1 = seed_hi(V.seed);
                 s = V.first + (uint32_t)(j - __ldg(a.qstart + qi));
@@ -532,7 +536,10 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
         const unsigned long long xs = (unsigned long long)x;
         const uint4 vr = active ? __ldg(vrec + cur) : make_uint4(0u, 0u, 0u, 0u);
         const int32_t d = (int32_t)vr.y;
-        bool live = active && d > 0;                 // group-uniform
+        // in-edges of equal weight u: the pick is edge floor(x / u), no search
+        // (the running sums and tree exist only when some vertex needs them)
+        const bool eqw = vr.w != 0u;
+        bool live = active && d > 0 && !eqw;         // group-uniform
         const uint32_t nlev = vr.z >> 28;
         const int lmax = (int)__reduce_max_sync(kFull, live ? nlev : 0u);
         const unsigned long long *lvl = tree + (vr.z & 0x0fffffffu);   // levels stored top-down
@@ -582,10 +589,18 @@ __global__ void __launch_bounds__(kSampleThreads, G == 32 ? 8 : 5) k_sample_lt(S
                 leaf = hv;
             }
         }
+        if (active && eqw) {
+            const uint32_t ei = x / vr.w;
+            if (ei < (uint32_t)d) {
+                pick = (int32_t)ei;
+                leaf = (unsigned long long)(uint32_t)__ldg(srcs + vr.x + ei);   // its source
+            }
+        }
         if (active && gl == 0) {
             sexam += (unsigned long long)(pick >= 0 ? pick + 1 : d);
-            // offsets, binary search of d cumulative weights, source, member write
-            sbytes += 16u + (d > 0 ? 8u * (uint32_t)(32 - __clz((uint32_t)d)) : 0u) +
+            // vertex record, binary search of d cumulative weights (none for equal
+            // weights), source, member write
+            sbytes += 16u + (d > 0 && !eqw ? 8u * (uint32_t)(32 - __clz((uint32_t)d)) : 0u) +
                       (pick >= 0 ? 4u : 0u) + 4u;
             if (sbytes > (1u << 30)) {   // only long walks of the second pass get here
                 abytes += sbytes;
@@ -1026,6 +1041,8 @@ __global__ void k_lt_tree_sizes(const int64_t *in_off, int64_t n, int32_t *sizes
 }
 
 // Vertices with at most 32 in-edges (no upper tree levels): one thread each.
+// The three index kernels write the vertex records and the flags always, and
+// the running sums (leaf) and tree levels only when leaf is non-null.
 __global__ void k_lt_index_small(const int64_t *in_off, const int32_t *in_src, const uint32_t *w,
                                  const int64_t *tree_off, unsigned long long *leaf, uint4 *vrec,
                                  int64_t n, int *invalid) {
@@ -1040,7 +1057,7 @@ __global__ void k_lt_index_small(const int64_t *in_off, const int32_t *in_src, c
             const uint32_t wi = w[i];
             same &= wi == w0;
             c += (unsigned long long)wi;
-            leaf[i] = (c << 31) | (unsigned long long)(uint32_t)in_src[i];
+            if (leaf) leaf[i] = (c << 31) | (unsigned long long)(uint32_t)in_src[i];
         }
         if (c > (1ull << 32)) atomicExch(invalid, 1);
         if (d > 0 && !(same && w0 != 0u)) invalid[2] = 1;   // the cut points are needed
@@ -1068,7 +1085,8 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
             same &= wi == w0;
             const unsigned long long x = i < e ? (unsigned long long)wi : 0ull;
             const unsigned long long incl = warp_incl_scan<unsigned long long>(x, lane);
-            if (i < e) leaf[i] = ((carry + incl) << 31) | (unsigned long long)(uint32_t)in_src[i];
+            if (leaf && i < e)
+                leaf[i] = ((carry + incl) << 31) | (unsigned long long)(uint32_t)in_src[i];
             carry += __shfl_sync(kFull, incl, 31);
         }
         same = __all_sync(kFull, same);
@@ -1080,6 +1098,7 @@ __global__ void k_lt_index(const int64_t *in_off, const int32_t *in_src, const u
             vrec[v] = make_uint4((uint32_t)b, (uint32_t)d,
                                  (uint32_t)tree_off[v] | ((uint32_t)L << 28), same ? w0 : 0u);
         __syncwarp();
+        if (!leaf) continue;
         // upper levels, top-down
         unsigned long long *lvl = tree + tree_off[v];
         for (int l = L; l >= 1; --l) {
@@ -1131,7 +1150,7 @@ __global__ void __launch_bounds__(256) k_lt_index_block(
             const unsigned long long off = carry + before + (incl - run);
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                if (i0 + q < e)
+                if (leaf && i0 + q < e)
                     leaf[i0 + q] = ((off + s[q]) << 31) | (unsigned long long)(uint32_t)in_src[i0 + q];
             carry += tot;
             __syncthreads();   // wsum is rewritten by the next pass
@@ -1145,6 +1164,7 @@ __global__ void __launch_bounds__(256) k_lt_index_block(
             vrec[v] = make_uint4((uint32_t)b, (uint32_t)d,
                                  (uint32_t)tree_off[v] | ((uint32_t)L << 28), same ? w0 : 0u);
         __syncthreads();   // every leaf of v written by the block is visible to it
+        if (!leaf) continue;   // (block-uniform)
         unsigned long long *lvl = tree + tree_off[v];
         for (int l = L; l >= 1; --l) {
             const int64_t sz = (d + (1ll << (5 * l)) - 1) >> (5 * l);
@@ -1568,7 +1588,7 @@ static std::mutex g_lt_index_mu;   // graphs are shared by serving workers
 
 im_status build_lt_index(im_graph *g, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_lt_index_mu);
-    if (g->lt_leaf) return IM_OK;   // set only once the whole index is built
+    if (g->lt_vrec) return IM_OK;   // set only once the whole index is built
     const int64_t n = g->n, m = g->m;
     // stream-ordered temporaries, freed on every exit
     struct Temps {
@@ -1615,10 +1635,9 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
         set_error("LT index: vertex list out of range");
         return IM_ERR_CUDA;
     }
-    IM_CUDA(cudaMalloc(&x.leaf, (size_t)std::max<int64_t>(m, 1) * 8));
-    IM_CUDA(cudaMalloc(&x.tree, (size_t)std::max<int64_t>(tree_total, 1) * 8));
     IM_CUDA(cudaMalloc(&x.vrec, (size_t)n * sizeof(uint4)));
-    {
+    // vertex records and flags; running sums and tree when leaf is set
+    auto index_pass = [&]() -> im_status {
         KernelTimer kt(st, "lt_index");
         k_lt_index_small<<<num_sms() * 8, 256, 0, st>>>(g->in_off, g->in_src, g->w, t.toff,
                                                         x.leaf, x.vrec, n, t.flags);
@@ -1628,14 +1647,23 @@ im_status build_lt_index(im_graph *g, cudaStream_t st) {
             k_lt_index_block<<<std::min(nbig, num_sms() * 8), 256, 0, st>>>(
                 g->in_off, g->in_src, g->w, t.toff, t.big, nbig, x.leaf, x.tree, x.vrec,
                 t.flags);
-    }
-    IM_CUDA(cudaGetLastError());
+        IM_CUDA(cudaGetLastError());
+        return IM_OK;
+    };
+    // first the vertex records alone: when every vertex's in-edges weigh the
+    // same (1/in-degree weights, for one) the walks pick by division and need
+    // neither running sums, tree nor cut points
+    IM_TRY(index_pass());
     int hflags[3] = {0, 0, 0};
     IM_CUDA(cudaMemcpyAsync(hflags, t.flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     IM_CUDA(cudaStreamSynchronize(st));
-    // the cut points serve only vertices whose in-edges weigh differently (or
-    // all zero): a graph without such vertices (1/in-degree weights) has none
     if (hflags[2] && m > 0) {
+        // some vertex's in-edges weigh differently (or all zero): the full
+        // index (the records are rewritten with the same values), then the cut
+        // points, which serve only such vertices
+        IM_CUDA(cudaMalloc(&x.leaf, (size_t)m * 8));
+        IM_CUDA(cudaMalloc(&x.tree, (size_t)std::max<int64_t>(tree_total, 1) * 8));
+        IM_TRY(index_pass());
         IM_CUDA(cudaMalloc(&x.guide, (size_t)m * sizeof(uint4)));
         {
             KernelTimer kt(st, "lt_index");
